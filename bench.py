@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 skeleton executor.
+
+Headline workload (one "step" = one execution of the skeleton on one input):
+  Map + MapReduce segmentation of a 512^3 uint8 volume (3-component mixture): the Map thresholds
+  into 3 classes written as uint8 labels, the MapReduce (+) produces int64 class counts (Section 4
+  of the paper, Segmentation). Algorithmic bytes per step: 128 MiB read + 128 MiB written + 24 B.
+  value = fused skeleton GB/s over all ranks; the kernel-per-stage version is timed beside it.
+Also measured in the same run (keys under "workloads"): the Filter Pipeline on 1024^2 and 8192^2,
+N-body (65536 bodies, 100 Loop iterations, GFLOP/s at 20 flop per interaction), and the batched
+4096-instance Filter Pipeline + 5x5 blur; each fused and kernel-per-stage.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrw|reference] [--no-extras]
+Under torchrun each rank runs its own replica on its own GPU (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused skeleton GB/s & % HBM peak vs kernel-per-stage; N-body GFLOP/s"
+SEG_SHAPE = (512, 512, 512)
+SEG_BYTES = 2 * 512 ** 3 + 24
+WORKLOAD = "segmentation 512^3 u8: Map(threshold 85/170 -> labels) + MapReduce(+) int64 class counts"
+
+
+# --------------------------------------------------------------------------------------------
+# clocks during the timed region (NVML through ctypes; read-only queries)
+# --------------------------------------------------------------------------------------------
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, device: int):
+        self.samples = []
+        self.max_mhz = None
+        self.ok = False
+        self._stop = threading.Event()
+        try:
+            import torch
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+            if self.nvml.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+                if self.nvml.nvmlDeviceGetHandleByIndex_v2(device, ctypes.byref(self.h)) != 0:
+                    return
+            m = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = m.value
+            self.reason_fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def sample(self):
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0 and \
+                self.reason_fn(self.h, ctypes.byref(r)) == 0:
+            self.samples.append((c.value, r.value))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self.sample()
+            time.sleep(0.002)
+
+    def start(self):
+        if self.ok:
+            self.sample()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+
+    def stop(self):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+            self.sample()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"]}
+        mhz = [s[0] for s in self.samples]
+        bits = 0
+        for s in self.samples:
+            bits |= s[1]
+        names = [n for b, n in REASONS.items() if bits & b and b != 0x1]
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": self.max_mhz, "reasons": names,
+                "samples": len(self.samples), "source": "nvml"}
+
+
+# --------------------------------------------------------------------------------------------
+# distributed helpers (one process per GPU; barrier + max over ranks)
+# --------------------------------------------------------------------------------------------
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def recorded_traffic(kernel_src: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(key)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1510_06585_gb300", "csrc", kernel_src)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["dram_bytes"] if rec.get("source_sha256_16") == h else None
+
+
+# --------------------------------------------------------------------------------------------
+# timing helpers
+# --------------------------------------------------------------------------------------------
+def time_steps(fn, steps, warmup, world, device, sampler=None):
+    """Run warmup then exactly `steps` timed calls of fn(i); returns (max-over-ranks seconds)."""
+    import torch
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    e0.record(s)
+    for i in range(steps):
+        fn(i)
+    e1.record(s)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.stop()
+    barrier(world)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device)
+
+
+def run_mrw(args):
+    import torch
+
+    from paper_1510_06585_gb300 import inputs
+    from paper_1510_06585_gb300 import mrw as M
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    M.load()
+    peaks, peak_src = load_peaks()
+    K, W = args.steps, args.warmup
+
+    # ---------------- headline: fused Map + MapReduce segmentation ----------------
+    vol = inputs.volume(*SEG_SHAPE)
+    sets = []
+    for _ in range(2):  # two input/output sets: 512 MiB in flight, > 2x the 129 MB L2
+        x = torch.from_numpy(vol).to(device)
+        y = torch.empty_like(x)
+        c = torch.zeros(3, dtype=torch.int64, device=device)
+        sets.append((x, y, c))
+    tree = M.mapreduce(M.map_(M.stage("threshold3")))
+    lib = M.load()
+    bufs = [M.buffers(*s) for s in sets]
+    stream = torch.cuda.current_stream().cuda_stream
+    fused_cfg = M.config()
+    unfused_cfg = M.config(fusion=M.MRW_FUSE_NONE)
+
+    # futures are released after the timed region (releasing one waits for its work)
+    pending = []
+
+    def step_async(cfg):
+        def f(i):
+            fut = ctypes.c_void_p()
+            M.check(lib.mrw_execute(tree.h, bufs[i & 1], 3, ctypes.byref(cfg), stream, ctypes.byref(fut)), "execute")
+            pending.append(fut)
+        return f
+
+    def drain():
+        for fut in pending:
+            s = lib.mrw_future_wait(fut, -1)
+            lib.mrw_future_release(fut)
+            M.check(s, "future")
+        pending.clear()
+
+    sampler = ClockSampler(local)
+    t_fused = time_steps(step_async(fused_cfg), K, W, world, device, sampler)
+    drain()
+    # correctness of what was timed
+    hist = np.bincount(np.digitize(vol.reshape(-1), [85, 170]), minlength=3).astype(np.int64)
+    for x, y, c in sets:
+        assert np.array_equal(c.cpu().numpy(), hist), "segmentation counts differ from the histogram"
+    t_unfused = time_steps(step_async(unfused_cfg), K, W, world, device)
+    drain()
+    fused_s = t_fused / K
+    unfused_s = t_unfused / K
+    value = world * SEG_BYTES * K / t_fused / 1e9
+
+    # ---------------- e2e: host buffers through the C ABI ----------------
+    hx = torch.from_numpy(vol).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    hc = torch.zeros(3, dtype=torch.int64).pin_memory()
+    hbuf = M.buffers(hx, hy, hc)
+
+    def e2e_step(i):
+        fut = ctypes.c_void_p()
+        M.check(lib.mrw_execute(tree.h, hbuf, 3, ctypes.byref(fused_cfg), stream, ctypes.byref(fut)), "execute")
+        pending.append(fut)
+
+    k_e2e = max(1, min(K, 50))
+    t_e2e = time_steps(e2e_step, k_e2e, min(W, 3), world, device)
+    drain()
+    assert np.array_equal(hc.numpy(), hist)
+    e2e_value = world * SEG_BYTES * k_e2e / t_e2e / 1e9
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(fused_s * 1e3, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic (seeded 3-component mixture volume)",
+        "config": {"workload": WORKLOAD, "shape": list(SEG_SHAPE), "l2": "2 rotating input/output sets, 512 MiB > 2x L2",
+                   "parallelism": f"replicas x{world}", "launch": "fused chain kernel, default config"},
+        "kernel_per_stage": {"value": round(world * SEG_BYTES * K / t_unfused / 1e9, 2), "unit": "GB/s",
+                             "ms_per_step": round(unfused_s * 1e3, 5),
+                             "speedup_fused": round(unfused_s / fused_s, 3)},
+        "roofline": {"bound": "hbm", "achieved": round(SEG_BYTES / fused_s / 1e9, 2), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(SEG_BYTES / fused_s / 1e9 / peaks["hbm_gbs"], 4),
+                     "traffic": recorded_traffic("k_chain.cu", "segmentation_512cubed_chain"),
+                     "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "note": "achieved = algorithmic bytes / CUDA-event time of the step (chain kernel + 24-byte memset)"},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
+                "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e},
+        "gpu_launches": K,
+        "clocks": sampler.summary(),
+    }
+
+    # ---------------- other workloads of the hot path ----------------
+    if args.extras:
+        result["workloads"] = extras(M, lib, device, world, stream, peaks, pending, drain)
+
+    # ---------------- CPU baseline (oracle) ----------------
+    if rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline(vol)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def extras(M, lib, device, world, stream, peaks, pending, drain):
+    import torch
+
+    from paper_1510_06585_gb300 import inputs
+    out = {}
+
+    def timed(fn, reps, warm=2):
+        for i in range(warm):
+            fn(i)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(reps):
+            fn(i)
+        e1.record()
+        torch.cuda.synchronize()
+        drain()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    def launcher(tree, bufsets, cfg):
+        def f(i):
+            fut = ctypes.c_void_p()
+            M.check(lib.mrw_execute(tree.h, bufsets[i % len(bufsets)], len(bufsets[0]), ctypes.byref(cfg), stream,
+                                    ctypes.byref(fut)), "execute")
+            pending.append(fut)
+        return f
+
+    fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
+    # Filter Pipeline (noise -> solarise -> mirror)
+    ftree = M.pipeline(M.stage("noise", seed=2), M.stage("solarise"), M.stage("mirror"))
+    for side, nsets in ((1024, 1), (8192, 2)):
+        img = inputs.filter_image(side, side)
+        sets = []
+        for _ in range(nsets):
+            x = torch.from_numpy(img).to(device)
+            sets.append(M.buffers(x, torch.empty_like(x)))
+        reps = 200 if side == 1024 else 20
+        tf = timed(launcher(ftree, sets, fused), reps)
+        tu = timed(launcher(ftree, sets, unfused), reps)
+        b = 2 * side * side
+        out[f"filter_{side}"] = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2),
+                                 "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
+                                 "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+                                 "l2": "resident (2 MiB)" if side == 1024 else "2 rotating sets, 256 MiB"}
+    # N-body: accel + Loop(100 KDK)
+    n = 65536
+    xs, vs, as_ = inputs.nbody(n)
+    st = [torch.from_numpy(t).to(device) for t in (xs, vs, as_)]
+    kdk = M.stage("nbody_kdk", eps=1e-3, dt=1e-3)
+    ntree = M.pipeline(M.stage("nbody_accel", eps=1e-3, dt=1e-3), M.loop(kdk, 100))
+    nb = [M.buffers(*st)]
+    tn = timed(launcher(ntree, nb, fused), 3, warm=1)
+    tnu = timed(launcher(ntree, nb, unfused), 1, warm=0)
+    inter = float(n) * n * 101
+    alu_peak = 20.0 * 152 * 128 * 2070e6 / 12 / 1e9  # GFLOP/s at 12 FP32-pipe instructions per interaction
+    gf = 20.0 * inter / tn / 1e9
+    out["nbody_65536x100"] = {"gflops": round(gf, 1), "ms": round(tn * 1e3, 2),
+                              "interactions_per_s": round(inter / tn, 1),
+                              "frac_alu": round(gf / alu_peak, 4), "alu_peak_gflops": round(alu_peak, 1),
+                              "kernel_per_step_host_loop_ms": round(tnu * 1e3, 2),
+                              "speedup_fused": round(tnu / tn, 3)}
+    # Batched: 4096 instances of Filter Pipeline + 5x5 blur
+    shapes = inputs.batch_shapes(4096)
+    desc, nbytes = inputs.batch_descriptors(shapes)
+    arena = inputs.batch_arena(desc, nbytes)
+    bx = torch.from_numpy(arena).to(device)
+    by = torch.zeros_like(bx)
+    btree = M.map_(M.pipeline(M.stage("noise"), M.stage("solarise"), M.stage("mirror"), M.stage("blur5")))
+    d = np.ascontiguousarray(desc, dtype=np.int64)
+    dptr = d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+    def blaunch(cfg):
+        def f(i):
+            fut = ctypes.c_void_p()
+            M.check(lib.mrw_execute_batched(btree.h, bx.data_ptr(), by.data_ptr(), bx.numel(), dptr, d.shape[0],
+                                            ctypes.byref(cfg), stream, ctypes.byref(fut)), "batched")
+            pending.append(fut)
+        return f
+
+    px = float((shapes[:, 0] * shapes[:, 1]).sum())
+    tb = timed(blaunch(fused), 5)
+    tbu = timed(blaunch(unfused), 3)
+    out["batched_4096"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
+                           "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
+                           "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
+                           "launches_per_step": 1}
+    return out
+
+
+def cpu_baseline(vol, min_seconds=8.0):
+    """The oracle as it stands on a bounded sample of the workload (the first 128 planes)."""
+    from oracle import image as O
+    sample = vol[:128]
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < min_seconds:
+        O.segmentation(sample)
+        reps += 1
+    dt = time.perf_counter() - t0
+    b = (2 * sample.size + 24) * reps
+    return {"value": round(b / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x Map+MapReduce on the first 128 of 512 planes (32 MiB), numpy single thread",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import image as O
+    from paper_1510_06585_gb300 import inputs
+    sample = inputs.volume(32, 512, 512)  # a bounded sample of the workload per step (8 MiB)
+    for _ in range(args.warmup):
+        O.segmentation(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.segmentation(sample)
+    dt = time.perf_counter() - t0
+    b = (2 * sample.size + 24) * args.steps
+    v = b / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded 3-component mixture volume)",
+            "config": {"workload": WORKLOAD + " (oracle on a 32-plane sample per step)", "shape": [32, 512, 512]},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "32 of 512 planes (8 MiB) per step, numpy single thread"},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mrw", choices=["mrw", "reference"])
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mrw":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mrw(args)
+
+
+if __name__ == "__main__":
+    main()

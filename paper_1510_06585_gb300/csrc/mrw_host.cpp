@@ -1,0 +1,2128 @@
+// Host runtime of the skeleton executor: the C ABI of include/mrw.h.
+//
+// Layers (Section 2 of the paper, re-cast for one GPU):
+//   Library  — skeleton tree construction (Table 1): mrw_stage / pipeline / map / mapreduce / loop;
+//   Scheduler— flattening the tree depth-first (Section 2, single-device execution model) into a
+//              program, validating it against the buffers and the partitioning constraints
+//              (Section 3.1), and grouping consecutive stages into fused kernels;
+//   Task launcher — enqueueing the groups on the caller's stream, staging host buffers, and
+//              returning a future backed by CUDA events (Section 2.1, run / Future);
+//   Auto tuner + knowledge base — timing candidate configurations (Algorithm 1, adapted) and
+//              recording the best per (tree, workload) (Section 3.2);
+//   Cost model — a small MLP trained on the tuner's timings that derives a configuration for an
+//              unseen pair (replacing the interpolation of Section 3.2, Configuration Derivation).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <random>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "mrw.h"
+#include "mrw_internal.h"
+
+using namespace mrw;
+
+// ============================================================================================
+// Errors
+// ============================================================================================
+namespace {
+thread_local std::string t_err;
+
+mrw_status fail(mrw_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+mrw_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();  // clear a non-sticky error so the stream stays usable
+  return fail(e == cudaErrorMemoryAllocation ? MRW_ERR_OOM : MRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    mrw_status s_ = (expr);        \
+    if (s_ != MRW_OK) return s_;   \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+std::mutex g_mu;  // guards the caches below
+
+struct DeviceInfo {
+  int sms = 0;
+};
+DeviceInfo device_info(int dev) {
+  static std::map<int, DeviceInfo> cache;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  DeviceInfo d;
+  cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (d.sms <= 0) d.sms = 1;
+  cache[dev] = d;
+  return d;
+}
+
+// ============================================================================================
+// Status slots: a device word kernels can set, and a pinned host word it is copied into
+// ============================================================================================
+struct StatusSlot {
+  unsigned int *dev = nullptr;
+  unsigned int *host = nullptr;
+  int idx = -1;
+  int block = -1;
+};
+
+class StatusPool {
+ public:
+  mrw_status take(StatusSlot *out) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.empty()) {
+      const int n = 1024;
+      unsigned int *d = nullptr, *h = nullptr;
+      CU(cudaMalloc(&d, n * sizeof(unsigned int)));
+      if (cudaHostAlloc(&h, n * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaFree(d);
+        return fail(MRW_ERR_OOM, "pinned status words");
+      }
+      const int b = (int)blocks_.size();
+      blocks_.push_back({d, h});
+      for (int i = n - 1; i >= 0; --i) free_.push_back({b, i});
+    }
+    auto [b, i] = free_.back();
+    free_.pop_back();
+    out->dev = blocks_[b].first + i;
+    out->host = blocks_[b].second + i;
+    out->idx = i;
+    out->block = b;
+    *out->host = 0;
+    return MRW_OK;
+  }
+  void give(const StatusSlot &s) {
+    if (s.idx < 0) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.push_back({s.block, s.idx});
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<std::pair<unsigned int *, unsigned int *>> blocks_;
+  std::vector<std::pair<int, int>> free_;
+};
+StatusPool &status_pool() {
+  static StatusPool p;
+  return p;
+}
+
+}  // namespace
+
+// ============================================================================================
+// Nodes (Section 2.1: SCT built bottom-up)
+// ============================================================================================
+enum NodeKind { N_STAGE = 0, N_PIPELINE = 1, N_MAP = 2, N_MAPREDUCE = 3, N_LOOP = 4 };
+
+struct mrw_node {
+  std::atomic<int> refs{1};
+  NodeKind kind = N_STAGE;
+  mrw_stage_kind stage = MRW_ST_NOISE_HASH;
+  mrw_stage_params params{};
+  std::vector<mrw_node *> kids;
+  mrw_reduce_op op = MRW_RED_ADD;
+  mrw_loop_state loop{};
+};
+
+struct mrw_future {
+  cudaEvent_t start = nullptr, done = nullptr;
+  int device = 0;
+  StatusSlot slot;
+  bool has_status = false;
+  mrw_status deferred = MRW_OK;  // an error found while enqueueing after the first launch
+};
+
+namespace {
+
+mrw_node *new_node(NodeKind k) {
+  mrw_node *n = new (std::nothrow) mrw_node();
+  if (n) n->kind = k;
+  return n;
+}
+
+void release_node(mrw_node *n) {
+  if (!n) return;
+  if (n->refs.fetch_sub(1) == 1) {
+    for (mrw_node *c : n->kids) release_node(c);
+    delete n;
+  }
+}
+
+bool contains(const mrw_node *root, const mrw_node *x) {
+  if (root == x) return true;
+  for (const mrw_node *c : root->kids)
+    if (contains(c, x)) return true;
+  return false;
+}
+
+bool valid_stage_kind(int k) { return k >= MRW_ST_NOISE_HASH && k <= MRW_ST_SAXPY; }
+
+mrw_stage_params default_params(mrw_stage_kind k, const mrw_stage_params *p) {
+  mrw_stage_params q{};
+  if (p) q = *p;
+  if (k == MRW_ST_THRESHOLD3 && q.t0 == 0 && q.t1 == 0) {
+    q.t0 = 85;
+    q.t1 = 170;
+  }
+  return q;
+}
+
+// Structural signature of a tree (the paper's SCT unique identifier, Section 3.2 profiles).
+void signature(const mrw_node *n, std::string &s) {
+  char buf[160];
+  switch (n->kind) {
+    case N_STAGE: {
+      const mrw_stage_params &p = n->params;
+      snprintf(buf, sizeof buf, "S%d{%u,%d,%d,%a,%a,%a,%a,%d,%d}", (int)n->stage, p.seed, p.t0, p.t1, p.G, p.eps,
+               p.dt, p.alpha, p.nu, p.wg);
+      s += buf;
+      return;
+    }
+    case N_PIPELINE: s += "P("; break;
+    case N_MAP: s += "M("; break;
+    case N_MAPREDUCE: snprintf(buf, sizeof buf, "R%d(", (int)n->op); s += buf; break;
+    case N_LOOP: snprintf(buf, sizeof buf, "L%lld,%d(", (long long)n->loop.max_iters, n->loop.kind); s += buf; break;
+  }
+  for (size_t i = 0; i < n->kids.size(); ++i) {
+    if (i) s += ",";
+    signature(n->kids[i], s);
+  }
+  s += ")";
+}
+
+// ============================================================================================
+// Programs: the tree flattened depth-first (Section 2, single-device execution model)
+// ============================================================================================
+enum Family { F_NONE = 0, F_IMAGE = 1, F_NBODY = 2, F_SAXPY = 3 };
+
+struct ImgStage {
+  int kind;  // OpKind
+  uint32_t seed;
+  uint32_t t;
+  int nu, wg;
+};
+
+struct NbStep {
+  int accel;  // 1: NBODY_ACCEL, 0: KDK steps
+  int64_t iters;
+  bool from_loop;
+  float G, eps, dt;
+  int nu, wg;
+};
+
+struct Program {
+  Family fam = F_NONE;
+  std::vector<ImgStage> img;
+  int reduce = RED_NONE;
+  bool stencil_in_row_map = false;  // a blur inside a Map whose partition is smaller than a plane
+  bool has_map = false;
+  std::vector<NbStep> nb;
+  std::vector<float> alphas;
+  int nu = 0, wg = 0;
+};
+
+mrw_status set_family(Program &p, Family f) {
+  if (p.fam == F_NONE) p.fam = f;
+  if (p.fam != f) return fail(MRW_ERR_UNSUPPORTED, "a tree mixes image, N-body and saxpy stages");
+  return MRW_OK;
+}
+
+int op_kind_of(mrw_stage_kind k) {
+  switch (k) {
+    case MRW_ST_NOISE_HASH: return OP_NOISE;
+    case MRW_ST_SOLARISE: return OP_SOLARISE;
+    case MRW_ST_MIRROR_H: return OP_MIRROR;
+    case MRW_ST_BOXBLUR5: return OP_BLUR;
+    case MRW_ST_THRESHOLD3: return OP_THRESH;
+    default: return -1;
+  }
+}
+
+const mrw_node *last_leaf(const mrw_node *n) {
+  while (n->kind != N_STAGE) {
+    if (n->kids.empty()) return nullptr;
+    n = n->kids.back();
+  }
+  return n;
+}
+
+mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64_t loop_mult) {
+  if (depth > 64) return fail(MRW_ERR_UNSUPPORTED, "tree deeper than 64 levels");
+  switch (n->kind) {
+    case N_STAGE: {
+      const mrw_stage_params &q = n->params;
+      if (q.nu < 0 || q.wg < 0 || (q.wg && (q.wg % 32 || q.wg > 1024)))
+        return fail(MRW_ERR_CONSTRAINT, "stage %d: wg must be a multiple of 32 up to 1024", (int)n->stage);
+      const int ok = op_kind_of(n->stage);
+      if (ok >= 0) {
+        TRY(set_family(p, F_IMAGE));
+        if ((int64_t)p.img.size() >= MRW_MAX_STAGES)
+          return fail(MRW_ERR_UNSUPPORTED, "more than %d image stages after unrolling loops", MRW_MAX_STAGES);
+        if (n->stage == MRW_ST_THRESHOLD3 && (q.t0 < 0 || q.t0 > 255 || q.t1 < 0 || q.t1 > 255))
+          return fail(MRW_ERR_INVALID_ARG, "threshold outside [0, 255]");
+        p.img.push_back({ok, q.seed, (uint32_t)(q.t0 & 0xFF) | ((uint32_t)(q.t1 & 0xFF) << 8), q.nu, q.wg});
+      } else if (n->stage == MRW_ST_NBODY_ACCEL || n->stage == MRW_ST_NBODY_KDK) {
+        TRY(set_family(p, F_NBODY));
+        if (!(q.eps > 0.f) || !std::isfinite(q.eps) || !std::isfinite(q.G) || !std::isfinite(q.dt) || q.G < 0.f)
+          return fail(MRW_ERR_INVALID_ARG, "N-body stage needs finite G >= 0, dt and eps > 0");
+        const bool accel = n->stage == MRW_ST_NBODY_ACCEL;
+        if (!accel && !p.nb.empty() && !p.nb.back().accel && p.nb.back().G == q.G && p.nb.back().eps == q.eps &&
+            p.nb.back().dt == q.dt && p.nb.back().from_loop == (loop_mult > 1)) {
+          p.nb.back().iters += loop_mult;
+        } else {
+          p.nb.push_back({accel ? 1 : 0, accel ? 1 : loop_mult, loop_mult > 1 || !is_root, q.G, q.eps, q.dt, q.nu,
+                          q.wg});
+          if (accel && loop_mult > 1) return fail(MRW_ERR_UNSUPPORTED, "NBODY_ACCEL inside a Loop");
+        }
+      } else if (n->stage == MRW_ST_SAXPY) {
+        TRY(set_family(p, F_SAXPY));
+        for (int64_t i = 0; i < loop_mult; ++i) p.alphas.push_back(q.alpha);
+      } else {
+        return fail(MRW_ERR_INVALID_ARG, "unknown stage kind %d", (int)n->stage);
+      }
+      if (q.nu) p.nu = q.nu;
+      if (q.wg) p.wg = q.wg;
+      return MRW_OK;
+    }
+    case N_PIPELINE:
+      if (n->kids.empty()) return fail(MRW_ERR_INVALID_ARG, "empty pipeline");
+      for (const mrw_node *c : n->kids) TRY(flatten(c, p, depth + 1, false, loop_mult));
+      return MRW_OK;
+    case N_MAP:
+      p.has_map = true;
+      return flatten(n->kids[0], p, depth + 1, false, loop_mult);
+    case N_MAPREDUCE: {
+      if (!is_root) return fail(MRW_ERR_UNSUPPORTED, "MapReduce must be the root of the executed tree");
+      if (n->op != MRW_RED_ADD)
+        return fail(MRW_ERR_UNSUPPORTED, "the device path implements the + merging function only");
+      p.has_map = true;
+      TRY(flatten(n->kids[0], p, depth + 1, false, loop_mult));
+      if (p.fam != F_IMAGE) return fail(MRW_ERR_UNSUPPORTED, "MapReduce over a non-image map");
+      const mrw_node *leaf = last_leaf(n->kids[0]);
+      p.reduce = (leaf && leaf->stage == MRW_ST_THRESHOLD3) ? RED_COUNT3 : RED_SUM;
+      return MRW_OK;
+    }
+    case N_LOOP: {
+      const mrw_loop_state &st = n->loop;
+      if (st.max_iters < 0 || st.max_iters > 100000000) return fail(MRW_ERR_INVALID_ARG, "loop max_iters out of range");
+      if (st.kind != MRW_LOOP_FOR) return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", st.kind);
+      if (st.max_iters == 0) return MRW_OK;
+      if (loop_mult > 1 && st.max_iters > 1)
+        return fail(MRW_ERR_UNSUPPORTED, "nested loops with more than one iteration each");
+      Program probe;
+      TRY(flatten(n->kids[0], probe, depth + 1, false, 1));
+      if (probe.fam == F_IMAGE || probe.fam == F_SAXPY) {
+        // pointwise / stencil bodies: iterations become consecutive stages (fused across iterations)
+        for (int64_t i = 0; i < st.max_iters; ++i) TRY(flatten(n->kids[0], p, depth + 1, false, 1));
+        return MRW_OK;
+      }
+      if (probe.fam == F_NBODY) {
+        for (const NbStep &s : probe.nb)
+          if (s.accel) return fail(MRW_ERR_UNSUPPORTED, "NBODY_ACCEL inside a Loop (the body must be KDK steps)");
+        return flatten(n->kids[0], p, depth + 1, false, st.max_iters * loop_mult);
+      }
+      return MRW_OK;
+    }
+  }
+  return fail(MRW_ERR_INVALID_ARG, "bad node");
+}
+
+// ============================================================================================
+// Configurations: 16 candidates per family (the tuner's and the cost model's index space)
+// ============================================================================================
+struct Shape {
+  int block, cps, unroll, tile_h, tile_w, bpt;
+};
+const Shape kShapes[8] = {
+    {256, 8, 4, 32, 128, 2},   // default
+    {256, 4, 2, 16, 128, 1},
+    {128, 8, 8, 32, 64, 4},
+    {512, 2, 4, 64, 64, 2},
+    {256, 2, 1, 8, 256, 1},
+    {128, 16, 2, 16, 64, 4},
+    {256, 1, 8, 64, 128, 2},
+    {1024, 1, 4, 32, 256, 4},
+};
+const int kNbodyCps[8] = {1, 1, 1, 2, 2, 2, 4, 4};
+
+mrw_config candidate(int i) {
+  mrw_config c{};
+  const Shape &s = kShapes[i % 8];
+  c.fusion = i < 8 ? MRW_FUSE_ALL : MRW_FUSE_NONE;
+  c.block = s.block;
+  c.ctas_per_sm = s.cps;
+  c.unroll = s.unroll;
+  c.tile_rows = s.tile_h;
+  c.tile_cols = s.tile_w;
+  return c;
+}
+
+mrw_config nbody_candidate(int i) {
+  mrw_config c{};
+  const int s = i % 8;
+  c.fusion = i < 8 ? MRW_FUSE_ALL : MRW_FUSE_NONE;
+  c.block = 0;
+  c.ctas_per_sm = kNbodyCps[s];
+  c.tile_rows = (s % 3 == 0) ? 2 : (s % 3 == 1 ? 1 : 4);
+  c.tile_cols = 0;
+  c.unroll = 0;
+  return c;
+}
+
+mrw_config default_config(Family f) { return f == F_NBODY ? nbody_candidate(0) : candidate(0); }
+
+mrw_status check_config(const mrw_config &c) {
+  if (c.fusion != MRW_FUSE_ALL && c.fusion != MRW_FUSE_NONE) return fail(MRW_ERR_INVALID_ARG, "bad fusion mode");
+  if (c.block && (c.block % 32 || c.block < 32 || c.block > 1024)) return fail(MRW_ERR_INVALID_ARG, "bad block");
+  if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return fail(MRW_ERR_INVALID_ARG, "bad ctas_per_sm");
+  if (c.unroll && c.unroll != 1 && c.unroll != 2 && c.unroll != 4 && c.unroll != 8)
+    return fail(MRW_ERR_INVALID_ARG, "unroll must be 1, 2, 4 or 8");
+  if (c.tile_rows < 0 || c.tile_rows > 252 || c.tile_cols < 0 || c.tile_cols > 224 || c.tile_cols % 16)
+    return fail(MRW_ERR_INVALID_ARG, "bad tile shape");
+  if (c.reserved[0] || c.reserved[1]) return fail(MRW_ERR_INVALID_ARG, "reserved config fields must be 0");
+  return MRW_OK;
+}
+
+// ============================================================================================
+// Buffers and argument validation
+// ============================================================================================
+int64_t elem_size(mrw_dtype t) {
+  switch (t) {
+    case MRW_U8: return 1;
+    case MRW_BF16: return 2;
+    case MRW_I32: case MRW_F32: return 4;
+    case MRW_I64: case MRW_F64: return 8;
+  }
+  return 0;
+}
+
+struct View {       // a resolved 2-D view: rows of `width` elements, `pitch` bytes apart
+  const mrw_buffer *b;
+  int64_t width, rows, pitch, esize;
+  int64_t numel() const { return width * rows; }
+};
+
+mrw_status view_of(const mrw_buffer &b, int idx, View *v) {
+  if (!b.data) return fail(MRW_ERR_INVALID_ARG, "args[%d].data is NULL", idx);
+  if (b.ndim < 1 || b.ndim > MRW_MAX_DIMS) return fail(MRW_ERR_SHAPE, "args[%d].ndim = %d", idx, b.ndim);
+  const int64_t es = elem_size(b.dtype);
+  if (!es) return fail(MRW_ERR_DTYPE, "args[%d]: unknown dtype", idx);
+  if (b.memory != MRW_MEM_DEVICE && b.memory != MRW_MEM_HOST)
+    return fail(MRW_ERR_INVALID_ARG, "args[%d]: bad memory kind", idx);
+  int64_t rows = 1;
+  for (int d = 0; d < b.ndim; ++d) {
+    if (b.shape[d] < 1) return fail(MRW_ERR_SHAPE, "args[%d].shape[%d] = %lld", idx, d, (long long)b.shape[d]);
+    if (d < b.ndim - 1) rows *= b.shape[d];
+  }
+  v->b = &b;
+  v->width = b.shape[b.ndim - 1];
+  v->rows = rows;
+  v->esize = es;
+  v->pitch = b.pitch ? b.pitch : v->width * es;
+  if (v->pitch < v->width * es) return fail(MRW_ERR_SHAPE, "args[%d]: pitch smaller than a row", idx);
+  return MRW_OK;
+}
+
+bool same_shape(const mrw_buffer &a, const mrw_buffer &b) {
+  if (a.ndim != b.ndim) return false;
+  for (int d = 0; d < a.ndim; ++d)
+    if (a.shape[d] != b.shape[d]) return false;
+  return true;
+}
+
+// ============================================================================================
+// Staging: device copies of host buffers, released after the call's work (stream ordered)
+// ============================================================================================
+struct Staged {
+  void *dev = nullptr;
+  int64_t pitch = 0;
+  bool copy_back = false;
+  View src;
+};
+
+struct Launch {  // everything one execute call enqueues
+  cudaStream_t stream;
+  int device;
+  int sms;
+  std::vector<void *> scratch;  // freed with cudaFreeAsync at the end
+  std::vector<Staged> staged;
+  mrw_future *fut = nullptr;
+
+  mrw_status alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    scratch.push_back(*p);
+    return MRW_OK;
+  }
+  void free_all() {
+    for (void *p : scratch) cudaFreeAsync(p, stream);
+    scratch.clear();
+  }
+};
+
+void configure_pool(int dev) {
+  static std::map<int, bool> done;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool between calls
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+// Device view of args[i]: the buffer itself, or a staged device copy (rows padded to 16 bytes).
+mrw_status resolve(Launch &L, const View &v, bool copy_in, bool copy_out, void **dev, int64_t *pitch) {
+  if (v.b->memory == MRW_MEM_DEVICE) {
+    *dev = v.b->data;
+    *pitch = v.pitch;
+    return MRW_OK;
+  }
+  Staged s;
+  s.src = v;
+  s.pitch = round_up(v.width * v.esize, 16);
+  TRY(L.alloc(&s.dev, (size_t)(s.pitch * v.rows)));
+  if (copy_in)
+    CU(cudaMemcpy2DAsync(s.dev, s.pitch, v.b->data, v.pitch, v.width * v.esize, v.rows, cudaMemcpyHostToDevice,
+                         L.stream));
+  s.copy_back = copy_out;
+  L.staged.push_back(s);
+  *dev = s.dev;
+  *pitch = s.pitch;
+  return MRW_OK;
+}
+
+mrw_status copy_back(Launch &L) {
+  for (const Staged &s : L.staged)
+    if (s.copy_back)
+      CU(cudaMemcpy2DAsync(s.src.b->data, s.src.pitch, s.dev, s.pitch, s.src.width * s.src.esize, s.src.rows,
+                           cudaMemcpyDeviceToHost, L.stream));
+  return MRW_OK;
+}
+
+
+// ============================================================================================
+// Image plans: consecutive stages grouped into fused kernels
+// ============================================================================================
+struct Group {
+  bool use_stencil = false;  // run by the stencil kernel (it has the blur, or the call is batched)
+  bool blur = false;
+  std::vector<ImgStage> pre, suf;  // pointwise stages before / after the blur
+  int reduce = RED_NONE;           // fused MapReduce (chain groups only)
+  bool reduce_only = false;        // a separate pass that reduces the previous group's output
+};
+
+int count_noise(const std::vector<ImgStage> &v) {
+  int c = 0;
+  for (const ImgStage &s : v) c += s.kind == OP_NOISE;
+  return c;
+}
+
+int mirror_parity(const std::vector<ImgStage> &v) {
+  int m = 0;
+  for (const ImgStage &s : v) m ^= (s.kind == OP_MIRROR);
+  return m;
+}
+
+// Fused: a group grows until a second blur, the op-count limit, or (chain groups) a third noise
+// stage; the blur's position splits the group into prefix and suffix. Unfused: one stage per group
+// (the kernel-per-stage execution), and a MapReduce reads the materialised labels in a pass of its own.
+std::vector<Group> group_stages(const Program &p, bool fused, bool batched) {
+  std::vector<Group> gs;
+  if (!fused) {
+    for (const ImgStage &s : p.img) {
+      Group g;
+      g.use_stencil = batched || s.kind == OP_BLUR;
+      g.blur = s.kind == OP_BLUR;
+      if (!g.blur) g.pre.push_back(s);
+      gs.push_back(g);
+    }
+  } else {
+    Group cur;
+    bool open = false;
+    auto fresh = [&]() {
+      cur = Group();
+      cur.use_stencil = batched;
+      open = true;
+    };
+    for (const ImgStage &s : p.img) {
+      if (!open) fresh();
+      if (s.kind == OP_BLUR) {
+        if (cur.blur) {
+          gs.push_back(cur);
+          fresh();
+        }
+        cur.blur = true;
+        cur.use_stencil = true;
+        continue;
+      }
+      std::vector<ImgStage> &list = cur.blur ? cur.suf : cur.pre;
+      const bool full = (int)list.size() >= kMaxChainOps ||
+                        (!cur.use_stencil && s.kind == OP_NOISE && count_noise(cur.pre) >= kMaxNoisePerGroup);
+      if (full) {
+        gs.push_back(cur);
+        fresh();
+      }
+      (cur.blur ? cur.suf : cur.pre).push_back(s);
+    }
+    if (open) gs.push_back(cur);
+  }
+  if (gs.empty()) {  // no stages: the output is a copy of the input
+    Group g;
+    g.use_stencil = batched;
+    gs.push_back(g);
+  }
+  if (p.reduce != RED_NONE) {
+    if (fused && !gs.back().use_stencil) {
+      gs.back().reduce = p.reduce;
+    } else {
+      Group r;
+      r.reduce_only = true;
+      r.reduce = p.reduce;
+      gs.push_back(r);
+    }
+  }
+  return gs;
+}
+
+void fill_ops(const std::vector<ImgStage> &v, int anchor_parity, ChainOp *ops) {
+  int before = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    ops[i].kind = v[i].kind;
+    ops[i].seed = v[i].seed;
+    ops[i].t = v[i].t;
+    ops[i].flip = anchor_parity ^ (before & 1);
+    before += v[i].kind == OP_MIRROR;
+  }
+}
+
+struct ImgGeom {
+  int64_t W, H, D, rows;
+};
+
+struct ChainShape {
+  int block, grid, unroll;
+  int64_t rows_parallel;
+};
+
+ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, int wg) {
+  ChainShape s;
+  int block = wg ? wg : (cfg.block ? cfg.block : 256);
+  int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
+  if (block > 256) {  // the chain kernel is compiled for at most 256 threads: keep threads per SM
+    cps = std::max(1, cps * block / 256);
+    block = 256;
+  }
+  const int64_t col_vecs = (W + 15) / 16;
+  const int64_t target = (int64_t)sms * cps * block;
+  s.rows_parallel = std::max<int64_t>(1, std::min<int64_t>(rows, target / col_vecs));
+  s.block = block;
+  s.grid = (int)((s.rows_parallel * col_vecs + block - 1) / block);
+  s.unroll = cfg.unroll ? cfg.unroll : 4;
+  return s;
+}
+
+mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op,
+                     const ImgGeom &geo, const mrw_config &cfg, int wg, unsigned long long *red) {
+  ChainArgs a{};
+  a.in = in;
+  a.out = g.reduce_only ? nullptr : out;
+  a.in_pitch = ip;
+  a.out_pitch = op;
+  a.rows = geo.rows;
+  a.W = (int32_t)geo.W;
+  a.col_vecs = (int32_t)((geo.W + 15) / 16);
+  a.nops = (int32_t)g.pre.size();
+  a.mirror = mirror_parity(g.pre);
+  fill_ops(g.pre, a.mirror, a.ops);
+  a.reduce = g.reduce;
+  a.red = red;
+  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg);
+  a.rows_parallel = s.rows_parallel;
+  CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+  return MRW_OK;
+}
+
+struct StencilShape {
+  int tile_h, tile_w, box_w, box_h, cps;
+  size_t smem;
+};
+
+StencilShape stencil_shape(const mrw_config &cfg, int halo) {
+  StencilShape s;
+  s.tile_h = cfg.tile_rows ? std::min(cfg.tile_rows, 252 - 2 * halo) : 32;
+  s.tile_w = cfg.tile_cols ? std::min(cfg.tile_cols, 224) : 128;
+  s.tile_w = std::max(16, s.tile_w / 16 * 16);
+  s.tile_h = std::max(1, s.tile_h);
+  s.box_w = (int)round_up(s.tile_w + 2 * halo + 15, 16);
+  s.box_h = s.tile_h + 2 * halo;
+  s.cps = std::min(8, cfg.ctas_per_sm ? cfg.ctas_per_sm : 4);
+  s.smem = stencil_smem_bytes(s.tile_h, s.tile_w, halo);
+  return s;
+}
+
+uint32_t test_wait_polls() {
+  const char *e = getenv("MRW_TEST_WAIT_POLLS");
+  return e ? (uint32_t)strtoul(e, nullptr, 10) : 0u;
+}
+
+void fill_stencil_ops(const Group &g, StencilArgs &a) {
+  a.wait_polls = test_wait_polls();
+  a.halo = g.blur ? 2 : 0;
+  a.npre = (int32_t)g.pre.size();
+  a.nsuf = (int32_t)g.suf.size();
+  a.mpre = mirror_parity(g.pre);
+  a.msuf = mirror_parity(g.suf);
+  fill_ops(g.pre, a.mpre, a.pre);
+  fill_ops(g.suf, a.msuf, a.suf);
+}
+
+// Device tables of a stencil launch: tensor maps, instances and the tile prefix sum.
+struct StencilTables {
+  std::vector<CUtensorMap> maps;
+  std::vector<StencilInstance> inst;
+  std::vector<int64_t> prefix;
+  int64_t total = 0;
+};
+
+mrw_status upload_tables(Launch &L, const StencilTables &t, void **dev_maps, void **dev_inst, void **dev_prefix,
+                         bool persistent, std::vector<void *> *owned) {
+  const size_t mb = t.maps.size() * sizeof(CUtensorMap), ib = t.inst.size() * sizeof(StencilInstance),
+               pb = t.prefix.size() * sizeof(int64_t);
+  const size_t off_i = round_up((int64_t)mb, 256), off_p = off_i + round_up((int64_t)ib, 256);
+  void *base = nullptr;
+  if (persistent) {
+    CU(cudaMalloc(&base, off_p + pb));
+    owned->push_back(base);
+  } else {
+    TRY(L.alloc(&base, off_p + pb));
+  }
+  std::vector<uint8_t> host(off_p + pb);
+  memcpy(host.data(), t.maps.data(), mb);
+  memcpy(host.data() + off_i, t.inst.data(), ib);
+  memcpy(host.data() + off_p, t.prefix.data(), pb);
+  CU(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, L.stream));
+  if (persistent) CU(cudaStreamSynchronize(L.stream));  // `host` dies at return
+  *dev_maps = base;
+  *dev_inst = (uint8_t *)base + off_i;
+  *dev_prefix = (uint8_t *)base + off_p;
+  return MRW_OK;
+}
+
+mrw_status run_stencil_single(Launch &L, const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op,
+                              const ImgGeom &geo, const mrw_config &cfg, unsigned int *status) {
+  StencilArgs a{};
+  fill_stencil_ops(g, a);
+  const StencilShape s = stencil_shape(cfg, a.halo);
+  StencilTables t;
+  t.maps.resize(1);
+  CU(encode_u8_map(&t.maps[0], in, geo.W, geo.H, geo.D, ip, s.box_w, s.box_h));
+  StencilInstance inst{};
+  inst.in_off = 0;
+  inst.out_off = 0;
+  inst.W = (int32_t)geo.W;
+  inst.H = (int32_t)geo.H;
+  inst.D = (int32_t)geo.D;
+  inst.pitch_in = (int32_t)ip;
+  inst.pitch_out = (int32_t)op;
+  inst.tiles_x = (int32_t)((geo.W + s.tile_w - 1) / s.tile_w);
+  inst.tiles_y = (int32_t)((geo.H + s.tile_h - 1) / s.tile_h);
+  inst.tile_base = 0;
+  t.inst.push_back(inst);
+  t.total = (int64_t)inst.tiles_x * inst.tiles_y * geo.D;
+  t.prefix = {0, t.total};
+  if (t.total >= (int64_t)UINT32_MAX - 1) return fail(MRW_ERR_UNSUPPORTED, "too many tiles");
+  void *dm, *di, *dp;
+  TRY(upload_tables(L, t, &dm, &di, &dp, false, nullptr));
+  void *q;
+  TRY(L.alloc(&q, 16));
+  CU(cudaMemsetAsync(q, 0, 16, L.stream));
+  a.maps = (const CUtensorMap *)dm;
+  a.inst = (const StencilInstance *)di;
+  a.tile_prefix = (const int64_t *)dp;
+  a.in_base = in;
+  a.out_base = out;
+  a.queue = (unsigned int *)q;
+  a.status = status;
+  a.total_tiles = t.total;
+  a.ninst = 1;
+  a.tile_h = s.tile_h;
+  a.tile_w = s.tile_w;
+  a.box_w = s.box_w;
+  a.box_h = s.box_h;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t.total, (int64_t)L.sms * s.cps));
+  CU(launch_stencil(a, grid, 256, s.smem, L.stream));
+  return MRW_OK;
+}
+
+mrw_status validate_image_args(const Program &p, const mrw_buffer *args, int nargs, View *vin, View *vout,
+                               View *vred) {
+  const int need = p.reduce != RED_NONE ? 3 : 2;
+  if (nargs != need) return fail(MRW_ERR_INVALID_ARG, "image tree takes %d arguments, got %d", need, nargs);
+  TRY(view_of(args[0], 0, vin));
+  TRY(view_of(args[1], 1, vout));
+  if (args[0].dtype != MRW_U8 || args[1].dtype != MRW_U8) return fail(MRW_ERR_DTYPE, "image stages read/write u8");
+  if (args[0].ndim < 2 || args[0].ndim > 3) return fail(MRW_ERR_SHAPE, "images are (H, W) or (D, H, W)");
+  if (!same_shape(args[0], args[1])) return fail(MRW_ERR_SHAPE, "input and output shapes differ");
+  if (vin->width > INT32_MAX / 2 || vin->rows > (int64_t)1 << 40) return fail(MRW_ERR_SHAPE, "image too large");
+  for (int i = 0; i < 2; ++i) {
+    const View &v = i ? *vout : *vin;
+    if (v.b->memory == MRW_MEM_DEVICE && ((uintptr_t)v.b->data % 16 || v.pitch % 16))
+      return fail(MRW_ERR_CONSTRAINT, "args[%d]: device images need a 16-byte aligned pointer and pitch", i);
+  }
+  // Partitioning constraints (Section 3.1): the elementary partitioning unit is a whole number of
+  // rows, and the per-thread element count nu divides it.
+  const int64_t plane = args[0].ndim == 3 ? args[0].shape[1] * vin->width : vin->rows * vin->width;
+  const int64_t epu = args[0].epu ? args[0].epu : plane;
+  if (epu % vin->width) return fail(MRW_ERR_CONSTRAINT, "epu %lld is not a whole number of rows", (long long)epu);
+  if (p.nu && epu % p.nu) return fail(MRW_ERR_CONSTRAINT, "epu %lld is not a multiple of nu %d", (long long)epu, p.nu);
+  bool blur = false;
+  for (const ImgStage &s : p.img) blur |= s.kind == OP_BLUR;
+  if (blur && p.has_map && epu % plane)
+    return fail(MRW_ERR_CONSTRAINT, "a stencil inside a Map needs whole planes as partitions");
+  // overlap: only a mirror-free, blur-free chain may run in place
+  if (vin->b->memory == MRW_MEM_DEVICE && vout->b->memory == MRW_MEM_DEVICE) {
+    const uintptr_t a0 = (uintptr_t)vin->b->data, a1 = a0 + vin->pitch * vin->rows;
+    const uintptr_t b0 = (uintptr_t)vout->b->data, b1 = b0 + vout->pitch * vout->rows;
+    const bool overlap = a0 < b1 && b0 < a1;
+    bool mirror = false;
+    for (const ImgStage &s : p.img) mirror |= s.kind == OP_MIRROR;
+    if (overlap && (a0 != b0 || vin->pitch != vout->pitch || mirror || blur))
+      return fail(MRW_ERR_INVALID_ARG, "output overlaps the input (only mirror- and blur-free chains run in place)");
+  }
+  if (p.reduce != RED_NONE) {
+    TRY(view_of(args[2], 2, vred));
+    const int64_t k = p.reduce == RED_COUNT3 ? 3 : 1;
+    if (args[2].dtype != MRW_I64) return fail(MRW_ERR_DTYPE, "the MapReduce result is int64");
+    if (vred->numel() != k) return fail(MRW_ERR_SHAPE, "the MapReduce result has %lld elements", (long long)k);
+  }
+  return MRW_OK;
+}
+
+ImgGeom geom_of(const mrw_buffer &b, const View &v) {
+  ImgGeom g;
+  g.W = v.width;
+  g.rows = v.rows;
+  if (b.ndim == 3) {
+    g.D = b.shape[0];
+    g.H = b.shape[1];
+  } else {
+    g.D = 1;
+    g.H = v.rows;
+  }
+  return g;
+}
+
+mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
+                         unsigned int *status, bool *used_status) {
+  View vin, vout, vred;
+  TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
+  const ImgGeom geo = geom_of(args[0], vin);
+  const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
+  void *din, *dout;
+  int64_t pin, pout;
+  TRY(resolve(L, vin, true, false, &din, &pin));
+  TRY(resolve(L, vout, false, true, &dout, &pout));
+  unsigned long long *red = nullptr;
+  void *dred = nullptr;
+  int64_t pred = 0;
+  if (p.reduce != RED_NONE) {
+    TRY(resolve(L, vred, false, true, &dred, &pred));
+    red = (unsigned long long *)dred;
+    CU(cudaMemsetAsync(red, 0, (size_t)(vred.numel() * 8), L.stream));
+  }
+  // intermediates between groups: at most two live at a time
+  bool any_stencil = false;
+  for (const Group &g : gs) any_stencil |= g.use_stencil;
+  if (any_stencil && status) CU(cudaMemsetAsync(status, 0, sizeof(unsigned int), L.stream));
+  const int64_t tpitch = round_up(geo.W, 16);
+  void *tmp[2] = {nullptr, nullptr};
+  int n_out_groups = 0;
+  for (const Group &g : gs) n_out_groups += !g.reduce_only;
+  if (n_out_groups > 1) TRY(L.alloc(&tmp[0], (size_t)(tpitch * geo.rows)));
+  if (n_out_groups > 2) TRY(L.alloc(&tmp[1], (size_t)(tpitch * geo.rows)));
+  const uint8_t *src = (const uint8_t *)din;
+  int64_t sp = pin;
+  int k = 0;
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const Group &g = gs[gi];
+    if (g.reduce_only) {
+      TRY(run_chain(L, g, src, sp, nullptr, 0, geo, cfg, p.wg, red));
+      continue;
+    }
+    ++k;
+    const bool last = k == n_out_groups;
+    uint8_t *dst = last ? (uint8_t *)dout : (uint8_t *)tmp[(k - 1) & 1];
+    const int64_t dp = last ? pout : tpitch;
+    if (g.use_stencil) {
+      TRY(run_stencil_single(L, g, src, sp, dst, dp, geo, cfg, status));
+      *used_status = true;
+    } else {
+      TRY(run_chain(L, g, src, sp, dst, dp, geo, cfg, p.wg, g.reduce != RED_NONE ? red : nullptr));
+    }
+    src = dst;
+    sp = dp;
+  }
+  return MRW_OK;
+}
+
+// ============================================================================================
+// N-body plans
+// ============================================================================================
+struct NbShape {
+  int grid, block, bpt;
+};
+
+NbShape nbody_shape(const mrw_config &cfg, int sms, int64_t n, int wg) {
+  NbShape s;
+  s.bpt = (cfg.tile_rows == 1 || cfg.tile_rows == 4) ? cfg.tile_rows : 2;
+  const int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 1;
+  int64_t grid = std::min<int64_t>((int64_t)sms * cps, std::max<int64_t>(1, (n + 32 * s.bpt - 1) / (32 * s.bpt)));
+  int64_t per = (n + grid - 1) / grid;
+  int64_t block = round_up((per + s.bpt - 1) / s.bpt, 32);
+  if (wg) block = wg;
+  if (block > 256) block = 256;
+  if (block * s.bpt * grid < n) grid = (n + block * s.bpt - 1) / (block * s.bpt);
+  s.grid = (int)grid;
+  s.block = (int)block;
+  return s;
+}
+
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  LoopCtrl *ctrl = nullptr;
+};
+
+std::map<std::string, LoopGraph> &loop_graphs() {
+  static std::map<std::string, LoopGraph> m;
+  return m;
+}
+
+mrw_status get_loop_graph(const NBodyParams &np, int64_t iters, const NbShape &s, int device, LoopGraph *out) {
+  char key[256];
+  snprintf(key, sizeof key, "%d|%p|%p|%p|%d|%a|%a|%a|%lld|%d|%d|%d", device, (void *)np.x, (void *)np.v,
+           (void *)np.a, np.n, np.G, np.eps2, np.dt, (long long)iters, s.bpt, s.grid, s.block);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = loop_graphs().find(key);
+  if (it != loop_graphs().end()) {
+    *out = it->second;
+    return MRW_OK;
+  }
+  LoopGraph g;
+  CU(cudaMalloc(&g.ctrl, sizeof(LoopCtrl)));
+  cudaError_t e = build_nbody_loop_graph(np, g.ctrl, iters, s.bpt, s.grid, s.block, &g.exec);
+  if (e != cudaSuccess) {
+    cudaFree(g.ctrl);
+    return cuda_fail(e, "building the Loop graph");
+  }
+  if (loop_graphs().size() > 64) {  // bound the cache: drop everything (waits for the device)
+    cudaDeviceSynchronize();
+    for (auto &kv : loop_graphs()) {
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaFree(kv.second.ctrl);
+    }
+    loop_graphs().clear();
+  }
+  loop_graphs()[key] = g;
+  *out = g;
+  return MRW_OK;
+}
+
+mrw_status validate_nbody_args(const mrw_buffer *args, int nargs, View *v) {
+  if (nargs != 3) return fail(MRW_ERR_INVALID_ARG, "N-body trees take x, v, a");
+  for (int i = 0; i < 3; ++i) {
+    TRY(view_of(args[i], i, &v[i]));
+    if (args[i].dtype != MRW_F32) return fail(MRW_ERR_DTYPE, "N-body state is float32");
+    if (args[i].ndim != 2 || args[i].shape[1] != 4) return fail(MRW_ERR_SHAPE, "N-body arrays are (N, 4)");
+    if (args[i].shape[0] != args[0].shape[0]) return fail(MRW_ERR_SHAPE, "x, v, a differ in N");
+    if (v[i].pitch != 16) return fail(MRW_ERR_SHAPE, "N-body arrays must be dense");
+    if (args[i].memory == MRW_MEM_DEVICE && (uintptr_t)args[i].data % 16)
+      return fail(MRW_ERR_CONSTRAINT, "N-body arrays need 16-byte alignment");
+    if (args[i].transfer != MRW_COPY && args[i].transfer != MRW_PARTITION)
+      return fail(MRW_ERR_INVALID_ARG, "bad transfer mode");
+  }
+  if (args[0].shape[0] > INT32_MAX) return fail(MRW_ERR_SHAPE, "too many bodies");
+  return MRW_OK;
+}
+
+mrw_status enqueue_nbody(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg) {
+  View v[3];
+  TRY(validate_nbody_args(args, nargs, v));
+  const int64_t n = args[0].shape[0];
+  void *d[3];
+  int64_t pitch;
+  for (int i = 0; i < 3; ++i) TRY(resolve(L, v[i], true, true, &d[i], &pitch));
+  NBodyParams np;
+  np.x = (float4 *)d[0];
+  np.v = (float4 *)d[1];
+  np.a = (float4 *)d[2];
+  np.n = (int32_t)n;
+  const NbShape s = nbody_shape(cfg, L.sms, n, p.wg);
+  for (const NbStep &st : p.nb) {
+    np.G = st.G > 0.f ? st.G : (float)(1.0 / (double)n);
+    np.eps2 = st.eps * st.eps;
+    np.dt = st.dt;
+    if (st.accel) {
+      CU(launch_nbody_force(np, 0, s.bpt, s.grid, s.block, L.stream));
+      continue;
+    }
+    if (cfg.fusion == MRW_FUSE_NONE) {
+      // kernel per step and host-evaluated loop condition (the paper's Loop, Section 3.1)
+      for (int64_t it = 0; it < st.iters; ++it) {
+        CU(launch_nbody_drift(np, L.stream));
+        CU(launch_nbody_force(np, 0, s.bpt, s.grid, s.block, L.stream));
+        CU(launch_nbody_kick(np, L.stream));
+        if (st.from_loop) CU(cudaStreamSynchronize(L.stream));
+      }
+    } else if (st.from_loop) {
+      LoopGraph g;
+      TRY(get_loop_graph(np, st.iters, s, L.device, &g));
+      CU(cudaGraphLaunch(g.exec, L.stream));
+    } else {
+      for (int64_t it = 0; it < st.iters; ++it) {
+        CU(launch_nbody_drift(np, L.stream));
+        CU(launch_nbody_force(np, 1, s.bpt, s.grid, s.block, L.stream));
+      }
+    }
+  }
+  return MRW_OK;
+}
+
+// ============================================================================================
+// Saxpy
+// ============================================================================================
+mrw_status validate_saxpy_args(const mrw_buffer *args, int nargs, View *vx, View *vy) {
+  if (nargs != 2) return fail(MRW_ERR_INVALID_ARG, "saxpy takes x, y");
+  TRY(view_of(args[0], 0, vx));
+  TRY(view_of(args[1], 1, vy));
+  if (args[0].dtype != MRW_F32 || args[1].dtype != MRW_F32) return fail(MRW_ERR_DTYPE, "saxpy is float32");
+  if (vx->numel() != vy->numel()) return fail(MRW_ERR_SHAPE, "x and y differ in size");
+  if (vx->pitch != vx->width * 4 || vy->pitch != vy->width * 4) return fail(MRW_ERR_SHAPE, "saxpy vectors must be dense");
+  for (int i = 0; i < 2; ++i)
+    if (args[i].memory == MRW_MEM_DEVICE && (uintptr_t)args[i].data % 16)
+      return fail(MRW_ERR_CONSTRAINT, "saxpy vectors need 16-byte alignment");
+  return MRW_OK;
+}
+
+mrw_status enqueue_saxpy(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg) {
+  View vx, vy;
+  TRY(validate_saxpy_args(args, nargs, &vx, &vy));
+  void *dx, *dy;
+  int64_t pp;
+  TRY(resolve(L, vx, true, false, &dx, &pp));
+  TRY(resolve(L, vy, true, true, &dy, &pp));
+  const int block = p.wg ? p.wg : (cfg.block ? cfg.block : 256);
+  const int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
+  const int64_t n = vx.numel();
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)L.sms * cps * std::max(1, 256 / block),
+                                                                (n / 4 + block - 1) / block));
+  for (float a : p.alphas) CU(launch_saxpy((const float *)dx, (float *)dy, n, a, grid, block, L.stream));
+  return MRW_OK;
+}
+
+// ============================================================================================
+// Knowledge base (Section 3.2: profiles of past executions)
+// ============================================================================================
+struct KbRecord {
+  mrw_config cfg;
+  float ms;
+  int source;  // 0 exhaustive, 1 pruned, 2 model
+};
+std::map<std::string, KbRecord> &kb() {
+  static std::map<std::string, KbRecord> m;
+  return m;
+}
+
+std::string workload_signature(const mrw_buffer *args, int nargs) {
+  std::string s;
+  char buf[128];
+  for (int i = 0; i < nargs; ++i) {
+    snprintf(buf, sizeof buf, "%d:%d:", (int)args[i].dtype, args[i].ndim);
+    s += buf;
+    for (int d = 0; d < args[i].ndim && d < MRW_MAX_DIMS; ++d) {
+      snprintf(buf, sizeof buf, "%lldx", (long long)args[i].shape[d]);
+      s += buf;
+    }
+    snprintf(buf, sizeof buf, "p%lld;", (long long)args[i].pitch);
+    s += buf;
+  }
+  return s;
+}
+
+std::string tree_signature(const mrw_node *n) {
+  std::string s;
+  signature(n, s);
+  return s;
+}
+
+struct ModelSlot {
+  mrw_model *model = nullptr;
+  std::vector<mrw_config> cfgs;
+};
+ModelSlot &installed_model() {
+  static ModelSlot m;
+  return m;
+}
+
+}  // namespace
+
+// ============================================================================================
+// Cost model object
+// ============================================================================================
+struct mrw_model {
+  MlpDims d{};
+  int device = 0;
+  float *master = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr, *loss = nullptr;
+  uint16_t *bf = nullptr;
+  int32_t *idx = nullptr;
+  int64_t idx_cap = 0;
+  int64_t step = 0;
+};
+
+namespace {
+
+mrw_status get_program(const mrw_node *root, Program *p) {
+  if (!root) return fail(MRW_ERR_INVALID_ARG, "root is NULL");
+  TRY(flatten(root, *p, 0, true, 1));
+  if (p->fam == F_NONE) return fail(MRW_ERR_INVALID_ARG, "the tree has no stages");
+  return MRW_OK;
+}
+
+mrw_status model_predict(mrw_model *m, const float *feat, int *best);
+mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, float *f);
+
+// Argument checks of every family, before any CUDA call.
+mrw_status validate_args(const Program &p, const mrw_buffer *args, int nargs) {
+  if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
+  if (p.fam == F_IMAGE) {
+    View a, b, c;
+    return validate_image_args(p, args, nargs, &a, &b, &c);
+  }
+  if (p.fam == F_NBODY) {
+    View v[3];
+    return validate_nbody_args(args, nargs, v);
+  }
+  View x, y;
+  return validate_saxpy_args(args, nargs, &x, &y);
+}
+
+// Configuration for an execution without an explicit one: knowledge base, then the cost model
+// (recorded in the knowledge base as derived), then the default (Section 3.2, Fig. 4 decision).
+mrw_config pick_config(const mrw_node *root, const Program &p, const mrw_buffer *args, int nargs) {
+  const std::string key = tree_signature(root) + "|" + workload_signature(args, nargs);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = kb().find(key);
+    if (it != kb().end()) return it->second.cfg;
+  }
+  mrw_model *m = nullptr;
+  std::vector<mrw_config> cfgs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    m = installed_model().model;
+    cfgs = installed_model().cfgs;
+  }
+  if (m && (int)cfgs.size() == m->d.k) {
+    float f[MRW_NFEATURES];
+    int best = -1;
+    if (features_of(p, args, nargs, f) == MRW_OK && model_predict(m, f, &best) == MRW_OK && best >= 0) {
+      std::lock_guard<std::mutex> lk(g_mu);
+      kb()[key] = {cfgs[best], -1.f, 2};
+      return cfgs[best];
+    }
+  }
+  return default_config(p.fam);
+}
+
+// Enqueue one execution (no future); shared by mrw_execute and the tuner.
+mrw_status enqueue(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
+                   unsigned int *status, bool *used_status) {
+  TRY(check_config(cfg));
+  switch (p.fam) {
+    case F_IMAGE: TRY(enqueue_image(L, p, args, nargs, cfg, status, used_status)); break;
+    case F_NBODY: TRY(enqueue_nbody(L, p, args, nargs, cfg)); break;
+    case F_SAXPY: TRY(enqueue_saxpy(L, p, args, nargs, cfg)); break;
+    default: return fail(MRW_ERR_INVALID_ARG, "empty tree");
+  }
+  TRY(copy_back(L));
+  return MRW_OK;
+}
+
+mrw_status begin_launch(Launch &L, void *stream) {
+  L.stream = (cudaStream_t)stream;
+  CU(cudaGetDevice(&L.device));
+  L.sms = device_info(L.device).sms;
+  configure_pool(L.device);
+  return MRW_OK;
+}
+
+void free_future(mrw_future *f) {
+  if (!f) return;
+  if (f->start) cudaEventDestroy(f->start);
+  if (f->done) cudaEventDestroy(f->done);
+  status_pool().give(f->slot);
+  delete f;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+int32_t mrw_abi_version(void) { return MRW_ABI_VERSION; }
+
+const char *mrw_last_error(void) { return t_err.c_str(); }
+
+const char *mrw_status_string(mrw_status s) {
+  switch (s) {
+    case MRW_OK: return "ok";
+    case MRW_ERR_INVALID_ARG: return "invalid argument";
+    case MRW_ERR_SHAPE: return "shape mismatch";
+    case MRW_ERR_DTYPE: return "dtype mismatch";
+    case MRW_ERR_CONSTRAINT: return "partitioning constraint violated";
+    case MRW_ERR_OOM: return "out of memory";
+    case MRW_ERR_CUDA: return "CUDA error";
+    case MRW_ERR_TIMEOUT: return "timeout";
+    case MRW_ERR_DEVICE: return "device-side error";
+    case MRW_ERR_UNSUPPORTED: return "unsupported";
+    case MRW_ERR_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+mrw_status mrw_stage(mrw_stage_kind kind, const mrw_stage_params *params, mrw_node_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!valid_stage_kind(kind)) return fail(MRW_ERR_INVALID_ARG, "unknown stage kind %d", (int)kind);
+  mrw_node *n = new_node(N_STAGE);
+  if (!n) return fail(MRW_ERR_OOM, "node");
+  n->stage = kind;
+  n->params = default_params(kind, params);
+  *out = n;
+  return MRW_OK;
+}
+
+mrw_status mrw_pipeline_create(mrw_node_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = new_node(N_PIPELINE);
+  return *out ? MRW_OK : fail(MRW_ERR_OOM, "node");
+}
+
+mrw_status mrw_pipeline_add_node(mrw_node_t pipe, mrw_node_t child) {
+  if (!pipe || !child) return fail(MRW_ERR_INVALID_ARG, "NULL node");
+  if (pipe->kind != N_PIPELINE) return fail(MRW_ERR_INVALID_ARG, "not a pipeline");
+  if (contains(child, pipe)) return fail(MRW_ERR_INVALID_ARG, "adding a node to its own subtree");
+  child->refs.fetch_add(1);
+  pipe->kids.push_back(child);
+  return MRW_OK;
+}
+
+mrw_status mrw_pipeline_add_stage(mrw_node_t pipe, mrw_stage_kind kind, const mrw_stage_params *params) {
+  if (!pipe) return fail(MRW_ERR_INVALID_ARG, "NULL pipeline");
+  if (pipe->kind != N_PIPELINE) return fail(MRW_ERR_INVALID_ARG, "not a pipeline");
+  mrw_node_t st;
+  TRY(mrw_stage(kind, params, &st));
+  pipe->kids.push_back(st);  // the pipeline takes over the creation reference
+  return MRW_OK;
+}
+
+static mrw_status wrap(NodeKind k, mrw_node_t body, mrw_node_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!body) return fail(MRW_ERR_INVALID_ARG, "body is NULL");
+  mrw_node *n = new_node(k);
+  if (!n) return fail(MRW_ERR_OOM, "node");
+  body->refs.fetch_add(1);
+  n->kids.push_back(body);
+  *out = n;
+  return MRW_OK;
+}
+
+mrw_status mrw_map(mrw_node_t body, mrw_node_t *out) { return wrap(N_MAP, body, out); }
+
+mrw_status mrw_mapreduce(mrw_node_t map_body, mrw_reduce_op op, mrw_node_t *out) {
+  if (op < MRW_RED_ADD || op > MRW_RED_DIV) return fail(MRW_ERR_INVALID_ARG, "unknown merging function");
+  TRY(wrap(N_MAPREDUCE, map_body, out));
+  (*out)->op = op;
+  return MRW_OK;
+}
+
+mrw_status mrw_loop(mrw_node_t body, const mrw_loop_state *state, mrw_node_t *out) {
+  if (!state) return fail(MRW_ERR_INVALID_ARG, "state is NULL");
+  if (state->max_iters < 0 || state->max_iters > 100000000) return fail(MRW_ERR_INVALID_ARG, "max_iters out of range");
+  if (state->kind != MRW_LOOP_FOR) return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", state->kind);
+  TRY(wrap(N_LOOP, body, out));
+  (*out)->loop = *state;
+  return MRW_OK;
+}
+
+void mrw_node_retain(mrw_node_t n) {
+  if (n) n->refs.fetch_add(1);
+}
+
+void mrw_node_release(mrw_node_t n) { release_node(n); }
+
+mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg, void *stream,
+                       mrw_future_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
+  Program p;
+  TRY(get_program(root, &p));
+  TRY(validate_args(p, args, nargs));
+  const mrw_config c = cfg ? *cfg : pick_config(root, p, args, nargs);
+  TRY(check_config(c));
+  Launch L;
+  TRY(begin_launch(L, stream));
+  mrw_future *f = new (std::nothrow) mrw_future();
+  if (!f) return fail(MRW_ERR_OOM, "future");
+  f->device = L.device;
+  mrw_status s = status_pool().take(&f->slot);
+  if (s == MRW_OK && (cudaEventCreate(&f->start) != cudaSuccess || cudaEventCreate(&f->done) != cudaSuccess))
+    s = cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+  if (s != MRW_OK) {
+    free_future(f);
+    return s;
+  }
+  cudaEventRecord(f->start, L.stream);
+  bool used = false;
+  s = enqueue(L, p, args, nargs, c, f->slot.dev, &used);
+  if (used) cudaMemcpyAsync(f->slot.host, f->slot.dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, L.stream);
+  f->has_status = used;
+  L.free_all();
+  cudaEventRecord(f->done, L.stream);
+  if (s != MRW_OK) {
+    // what was enqueued still runs; wait for it so the future's resources can go
+    const std::string msg = t_err;
+    cudaEventSynchronize(f->done);
+    free_future(f);
+    t_err = msg;
+    return s;
+  }
+  *out = f;
+  return MRW_OK;
+}
+
+mrw_status mrw_future_query(mrw_future_t f) {
+  if (!f) return fail(MRW_ERR_INVALID_ARG, "future is NULL");
+  const cudaError_t e = cudaEventQuery(f->done);
+  if (e == cudaErrorNotReady) return MRW_ERR_NOT_READY;
+  if (e != cudaSuccess) return cuda_fail(e, "stream of the future");
+  if (f->has_status && *(volatile unsigned int *)f->slot.host != 0)
+    return fail(MRW_ERR_DEVICE, "a kernel gave up a bounded wait (status %u)", *f->slot.host);
+  return f->deferred;
+}
+
+mrw_status mrw_future_wait(mrw_future_t f, int64_t timeout_ms) {
+  if (!f) return fail(MRW_ERR_INVALID_ARG, "future is NULL");
+  if (timeout_ms < 0) {
+    const cudaError_t e = cudaEventSynchronize(f->done);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    return mrw_future_query(f);
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    const mrw_status s = mrw_future_query(f);
+    if (s != MRW_ERR_NOT_READY) return s;
+    const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+    if (el.count() >= timeout_ms) return fail(MRW_ERR_TIMEOUT, "future not complete after %lld ms", (long long)timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms) {
+  if (!f || !ms) return fail(MRW_ERR_INVALID_ARG, "NULL argument");
+  const cudaError_t e = cudaEventElapsedTime(ms, f->start, f->done);
+  if (e == cudaErrorNotReady) return MRW_ERR_NOT_READY;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+  return MRW_OK;
+}
+
+void mrw_future_release(mrw_future_t f) {
+  if (!f) return;
+  cudaEventSynchronize(f->done);  // the status slot must not be reused while a copy is pending
+  free_future(f);
+}
+
+// --------------------------------------------------------------------------------------------
+// Batched execution (pattern: thousands of uneven instances of one tree in one launch)
+// --------------------------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct BatchPlan {
+  std::vector<void *> owned;      // device tables (cudaMalloc)
+  void *tmp_arena[2] = {nullptr, nullptr};
+  unsigned int *counters = nullptr;  // one queue counter per group + a status word
+  cudaGraphExec_t exec = nullptr;
+  int ngroups = 0;
+};
+
+std::map<std::string, BatchPlan> &batch_plans() {
+  static std::map<std::string, BatchPlan> m;
+  return m;
+}
+
+void destroy_batch_plan(BatchPlan &b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  for (void *p : b.owned) cudaFree(p);
+  if (b.tmp_arena[0]) cudaFree(b.tmp_arena[0]);
+  if (b.tmp_arena[1]) cudaFree(b.tmp_arena[1]);
+  if (b.counters) cudaFree(b.counters);
+}
+
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const uint8_t *b = (const uint8_t *)p;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena, uint8_t *out_arena,
+                            int64_t arena_bytes, const int64_t *desc, int64_t n, const mrw_config &cfg,
+                            BatchPlan *bp) {
+  const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, true);
+  bp->ngroups = (int)gs.size();
+  CU(cudaMalloc(&bp->counters, sizeof(unsigned int) * (gs.size() + 1)));
+  if (gs.size() > 1) CU(cudaMalloc(&bp->tmp_arena[0], (size_t)arena_bytes));
+  if (gs.size() > 2) CU(cudaMalloc(&bp->tmp_arena[1], (size_t)arena_bytes));
+  CU(stencil_prepare());
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  Launch C = L;
+  C.stream = cs;
+  std::vector<StencilArgs> launches;
+  std::vector<int> grids;
+  std::vector<size_t> smems;
+  const uint8_t *src = in_arena;
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const Group &g = gs[gi];
+    StencilArgs a{};
+    fill_stencil_ops(g, a);
+    const StencilShape s = stencil_shape(cfg, a.halo);
+    uint8_t *dst = gi + 1 == gs.size() ? out_arena : (uint8_t *)bp->tmp_arena[gi & 1];
+    StencilTables t;
+    t.maps.resize((size_t)n);
+    t.inst.resize((size_t)n);
+    t.prefix.resize((size_t)n + 1);
+    int64_t tiles = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
+      const cudaError_t e = encode_u8_map(&t.maps[i], src + off, W, H, 1, pitch, s.box_w, s.box_h);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e, "encoding a tensor map");
+      }
+      StencilInstance &in = t.inst[i];
+      in.in_off = off;
+      in.out_off = off;
+      in.W = (int32_t)W;
+      in.H = (int32_t)H;
+      in.D = 1;
+      in.pitch_in = in.pitch_out = (int32_t)pitch;
+      in.seed_xor = (uint32_t)desc[5 * i + 4];
+      in.tiles_x = (int32_t)((W + s.tile_w - 1) / s.tile_w);
+      in.tiles_y = (int32_t)((H + s.tile_h - 1) / s.tile_h);
+      in.tile_base = tiles;
+      t.prefix[i] = tiles;
+      tiles += (int64_t)in.tiles_x * in.tiles_y;
+    }
+    t.prefix[n] = tiles;
+    t.total = tiles;
+    if (tiles >= (int64_t)UINT32_MAX - 1) {
+      cudaStreamDestroy(cs);
+      return fail(MRW_ERR_UNSUPPORTED, "too many tiles in one batch");
+    }
+    void *dm, *di, *dp;
+    mrw_status st = upload_tables(C, t, &dm, &di, &dp, true, &bp->owned);
+    if (st != MRW_OK) {
+      cudaStreamDestroy(cs);
+      return st;
+    }
+    a.maps = (const CUtensorMap *)dm;
+    a.inst = (const StencilInstance *)di;
+    a.tile_prefix = (const int64_t *)dp;
+    a.in_base = src;
+    a.out_base = dst;
+    a.queue = bp->counters + gi;
+    a.status = bp->counters + gs.size();
+    a.total_tiles = tiles;
+    a.ninst = (int32_t)n;
+    a.tile_h = s.tile_h;
+    a.tile_w = s.tile_w;
+    a.box_w = s.box_w;
+    a.box_h = s.box_h;
+    launches.push_back(a);
+    grids.push_back((int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)L.sms * s.cps)));
+    smems.push_back(s.smem);
+    src = dst;
+  }
+  // one graph: reset the counters, then the persistent launches
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(unsigned int) * (gs.size() + 1), cs);
+  for (size_t gi = 0; e == cudaSuccess && gi < launches.size(); ++gi)
+    e = launch_stencil(launches[gi], grids[gi], 256, smems[gi], cs);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "capturing the batched launch");
+  return MRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t *out_arena, int64_t arena_bytes,
+                               const int64_t *desc, int64_t n, const mrw_config *cfg, void *stream,
+                               mrw_future_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!in_arena || !out_arena || !desc || n <= 0 || arena_bytes <= 0)
+    return fail(MRW_ERR_INVALID_ARG, "batched call needs arenas, descriptors and n > 0");
+  if (n > (1 << 24)) return fail(MRW_ERR_INVALID_ARG, "too many instances");
+  if ((uintptr_t)in_arena % 16 || (uintptr_t)out_arena % 16)
+    return fail(MRW_ERR_CONSTRAINT, "arenas must be 16-byte aligned");
+  {
+    const uintptr_t a0 = (uintptr_t)in_arena, b0 = (uintptr_t)out_arena;
+    if (a0 < b0 + arena_bytes && b0 < a0 + arena_bytes) return fail(MRW_ERR_INVALID_ARG, "arenas overlap");
+  }
+  Program p;
+  TRY(get_program(root, &p));
+  if (p.fam != F_IMAGE) return fail(MRW_ERR_UNSUPPORTED, "batched execution runs image trees");
+  if (p.reduce != RED_NONE) return fail(MRW_ERR_UNSUPPORTED, "batched MapReduce");
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
+    if (W < 1 || H < 1 || W > (1 << 20) || H > (1 << 20)) return fail(MRW_ERR_SHAPE, "instance %lld: bad size", (long long)i);
+    if (off < 0 || off % 16 || pitch % 16 || pitch < W || pitch > INT32_MAX)
+      return fail(MRW_ERR_CONSTRAINT, "instance %lld: offset and pitch must be multiples of 16, pitch >= W",
+                  (long long)i);
+    if (off + H * pitch > arena_bytes) return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
+  }
+  mrw_config c = cfg ? *cfg : default_config(F_IMAGE);
+  TRY(check_config(c));
+  Launch L;
+  TRY(begin_launch(L, stream));
+  char keyb[256];
+  const uint64_t dh = hash_bytes(desc, (size_t)n * 5 * sizeof(int64_t));
+  snprintf(keyb, sizeof keyb, "%d|%p|%p|%p|%lld|%llx|%lld|%d,%d,%d,%d,%d,%d", L.device, (void *)stream,
+           (const void *)in_arena, (void *)out_arena, (long long)arena_bytes, (unsigned long long)dh, (long long)n,
+           c.fusion, c.block, c.ctas_per_sm, c.tile_rows, c.tile_cols, c.unroll);
+  const std::string key = tree_signature(root) + "|" + keyb;
+  BatchPlan plan;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = batch_plans().find(key);
+    if (it != batch_plans().end()) plan = it->second;
+  }
+  if (!plan.exec) {
+    mrw_status s = build_batch_plan(L, p, in_arena, out_arena, arena_bytes, desc, n, c, &plan);
+    if (s != MRW_OK) {
+      destroy_batch_plan(plan);
+      return s;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (batch_plans().size() >= 32) {
+      cudaDeviceSynchronize();
+      for (auto &kv : batch_plans()) destroy_batch_plan(kv.second);
+      batch_plans().clear();
+    }
+    batch_plans()[key] = plan;
+  }
+  mrw_future *f = new (std::nothrow) mrw_future();
+  if (!f) return fail(MRW_ERR_OOM, "future");
+  f->device = L.device;
+  mrw_status s = status_pool().take(&f->slot);
+  if (s == MRW_OK && (cudaEventCreate(&f->start) != cudaSuccess || cudaEventCreate(&f->done) != cudaSuccess))
+    s = cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+  if (s != MRW_OK) {
+    free_future(f);
+    return s;
+  }
+  cudaEventRecord(f->start, L.stream);
+  cudaError_t e = cudaGraphLaunch(plan.exec, L.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(f->slot.host, plan.counters + plan.ngroups, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                        L.stream);
+  f->has_status = true;
+  cudaEventRecord(f->done, L.stream);
+  if (e != cudaSuccess) {
+    cudaEventSynchronize(f->done);
+    free_future(f);
+    return cuda_fail(e, "launching the batched graph");
+  }
+  *out = f;
+  return MRW_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Plan description, features, tuner, knowledge base, cost model
+// ============================================================================================
+namespace {
+
+const char *op_name(int k) {
+  switch (k) {
+    case OP_NOISE: return "noise";
+    case OP_SOLARISE: return "solarise";
+    case OP_MIRROR: return "mirror";
+    case OP_BLUR: return "blur5";
+    case OP_THRESH: return "threshold3";
+  }
+  return "?";
+}
+
+void ops_json(std::ostringstream &o, const std::vector<ImgStage> &v) {
+  o << "[";
+  for (size_t i = 0; i < v.size(); ++i) o << (i ? "," : "") << "\"" << op_name(v[i].kind) << "\"";
+  o << "]";
+}
+
+mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const mrw_config &c, int sms,
+                    std::string *out) {
+  std::ostringstream o;
+  if (p.fam == F_IMAGE) {
+    View vin, vout, vred;
+    TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
+    const ImgGeom geo = geom_of(args[0], vin);
+    const std::vector<Group> gs = group_stages(p, c.fusion == MRW_FUSE_ALL, false);
+    o << "{\"family\":\"image\",\"W\":" << geo.W << ",\"H\":" << geo.H << ",\"D\":" << geo.D
+      << ",\"reduce\":" << p.reduce << ",\"groups\":[";
+    for (size_t i = 0; i < gs.size(); ++i) {
+      const Group &g = gs[i];
+      o << (i ? "," : "") << "{";
+      if (g.use_stencil) {
+        const StencilShape s = stencil_shape(c, g.blur ? 2 : 0);
+        const int64_t tx = (geo.W + s.tile_w - 1) / s.tile_w, ty = (geo.H + s.tile_h - 1) / s.tile_h;
+        o << "\"kernel\":\"stencil\",\"pre\":";
+        ops_json(o, g.pre);
+        o << ",\"blur\":" << (g.blur ? "true" : "false") << ",\"suf\":";
+        ops_json(o, g.suf);
+        o << ",\"tile\":[" << s.tile_h << "," << s.tile_w << "],\"box\":[" << s.box_h << "," << s.box_w
+          << "],\"tiles_x\":" << tx << ",\"tiles_y\":" << ty << ",\"tiles\":" << tx * ty * geo.D
+          << ",\"grid\":" << std::min<int64_t>(tx * ty * geo.D, (int64_t)sms * s.cps) << ",\"block\":256"
+          << ",\"smem\":" << s.smem;
+      } else {
+        const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg);
+        o << "\"kernel\":\"chain\",\"ops\":";
+        ops_json(o, g.pre);
+        o << ",\"reduce_only\":" << (g.reduce_only ? "true" : "false") << ",\"reduce\":" << g.reduce
+          << ",\"nu\":16,\"col_vecs\":" << (geo.W + 15) / 16 << ",\"rows_parallel\":" << s.rows_parallel
+          << ",\"grid\":" << s.grid << ",\"block\":" << s.block << ",\"unroll\":" << s.unroll;
+      }
+      o << "}";
+    }
+    o << "]}";
+  } else if (p.fam == F_NBODY) {
+    if (nargs != 3) return fail(MRW_ERR_INVALID_ARG, "N-body trees take x, v, a");
+    const int64_t n = args[0].shape[0];
+    const NbShape s = nbody_shape(c, sms, n, p.wg);
+    o << "{\"family\":\"nbody\",\"n\":" << n << ",\"grid\":" << s.grid << ",\"block\":" << s.block
+      << ",\"bodies_per_thread\":" << s.bpt << ",\"steps\":[";
+    for (size_t i = 0; i < p.nb.size(); ++i) {
+      const NbStep &st = p.nb[i];
+      o << (i ? "," : "") << "{\"kind\":\"" << (st.accel ? "accel" : "kdk") << "\",\"iters\":" << st.iters
+        << ",\"loop\":\""
+        << (st.accel ? "none" : (c.fusion == MRW_FUSE_NONE ? "host" : (st.from_loop ? "device_graph" : "unrolled")))
+        << "\"}";
+    }
+    o << "],\"partitions\":[";
+    for (int cta = 0; cta < s.grid; ++cta) {
+      const int64_t lo = n * cta / s.grid, hi = n * (cta + 1) / s.grid;
+      o << (cta ? "," : "") << "[" << lo << "," << hi - lo << "]";
+    }
+    o << "]}";
+  } else {
+    o << "{\"family\":\"saxpy\",\"stages\":" << p.alphas.size() << "}";
+  }
+  *out = o.str();
+  return MRW_OK;
+}
+
+float flog2(double v) { return v > 0 ? (float)std::log2(v) : 0.f; }
+
+mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, float *f) {
+  for (int i = 0; i < MRW_NFEATURES; ++i) f[i] = 0.f;
+  if (nargs < 1 || !args) return fail(MRW_ERR_INVALID_ARG, "features need the arguments");
+  View v;
+  TRY(view_of(args[0], 0, &v));
+  f[0] = p.fam == F_IMAGE;
+  f[1] = p.fam == F_SAXPY;
+  f[2] = p.fam == F_NBODY;
+  f[3] = p.reduce != RED_NONE;
+  int nn = 0, npw = 0, nm = 0, nb = 0;
+  for (const ImgStage &s : p.img) {
+    nn += s.kind == OP_NOISE;
+    npw += s.kind == OP_SOLARISE || s.kind == OP_THRESH;
+    nm += s.kind == OP_MIRROR;
+    nb += s.kind == OP_BLUR;
+  }
+  const double stages = p.fam == F_IMAGE ? (double)p.img.size() : (p.fam == F_SAXPY ? (double)p.alphas.size() : 0.0);
+  f[4] = (float)stages;
+  f[5] = (float)nn;
+  f[6] = (float)npw;
+  f[7] = (float)nm;
+  f[8] = (float)nb;
+  const double numel = (double)v.numel();
+  f[9] = flog2(numel);
+  f[10] = flog2((double)v.width);
+  f[11] = flog2((double)v.rows);
+  f[12] = (v.width * v.esize) % 16 != 0;
+  f[13] = (float)v.esize;
+  double bytes = 0, ops = 0;
+  if (p.fam == F_IMAGE) {
+    bytes = 2.0 * numel + (p.reduce ? 8.0 : 0.0);
+    ops = 20.0 * nn + 2.0 * npw + 15.0 * nb + 0.5 * nm;
+  } else if (p.fam == F_SAXPY) {
+    bytes = 12.0 * numel;
+    ops = 2.0 * stages;
+  } else {
+    bytes = 48.0 * numel;
+    ops = 20.0 * numel;
+  }
+  f[14] = flog2(bytes);
+  f[15] = (float)(ops / 16.0);
+  return MRW_OK;
+}
+
+std::vector<mrw_config> candidates_for(Family fam) {
+  std::vector<mrw_config> v;
+  for (int i = 0; i < 16; ++i) v.push_back(fam == F_NBODY ? nbody_candidate(i) : candidate(i));
+  return v;
+}
+
+// Median device time of `reps` executions of one configuration (after one warm-up).
+mrw_status time_config(const Program &p, const mrw_buffer *args, int nargs, const mrw_config &c, int reps,
+                       void *stream, unsigned int *status, float *ms) {
+  Launch L;
+  TRY(begin_launch(L, stream));
+  bool used = false;
+  mrw_status s = enqueue(L, p, args, nargs, c, status, &used);
+  L.free_all();
+  if (s != MRW_OK) return s;
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+  for (auto &e : ev) CU(cudaEventCreate(&e));
+  for (int r = 0; r < reps && s == MRW_OK; ++r) {
+    cudaEventRecord(ev[2 * r], L.stream);
+    s = enqueue(L, p, args, nargs, c, status, &used);
+    L.free_all();
+    cudaEventRecord(ev[2 * r + 1], L.stream);
+  }
+  const cudaError_t e = cudaStreamSynchronize(L.stream);
+  std::vector<float> t;
+  for (int r = 0; r < reps && s == MRW_OK && e == cudaSuccess; ++r) {
+    float x = 0;
+    cudaEventElapsedTime(&x, ev[2 * r], ev[2 * r + 1]);
+    t.push_back(x);
+  }
+  for (auto &ee : ev) cudaEventDestroy(ee);
+  if (e != cudaSuccess) return cuda_fail(e, "timing run");
+  if (s != MRW_OK) return s;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return MRW_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------------------------
+// Model helpers (host side)
+// --------------------------------------------------------------------------------------------
+namespace {
+
+mrw_status model_predict(mrw_model *m, const float *feat, int *best) {
+  int cur;
+  CU(cudaGetDevice(&cur));
+  if (cur != m->device) CU(cudaSetDevice(m->device));
+  float *buf = nullptr;
+  mrw_status s = MRW_OK;
+  cudaError_t e = cudaMalloc(&buf, sizeof(float) * (MRW_NFEATURES + m->d.k));
+  if (e == cudaSuccess) e = cudaMemcpy(buf, feat, sizeof(float) * MRW_NFEATURES, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_mlp_forward(m->d, m->bf, buf, 1, buf + MRW_NFEATURES, nullptr);
+  std::vector<float> y((size_t)m->d.k);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(y.data(), buf + MRW_NFEATURES, sizeof(float) * m->d.k, cudaMemcpyDeviceToHost);
+  if (buf) cudaFree(buf);
+  if (e != cudaSuccess) s = cuda_fail(e, "cost-model inference");
+  if (cur != m->device) cudaSetDevice(cur);
+  if (s != MRW_OK) return s;
+  *best = (int)(std::min_element(y.begin(), y.end()) - y.begin());
+  return MRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrw_status mrw_plan_describe(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
+                             char *buf, int64_t cap, int64_t *needed) {
+  Program p;
+  TRY(get_program(root, &p));
+  if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
+  const mrw_config c = cfg ? *cfg : pick_config(root, p, args, nargs);
+  TRY(check_config(c));
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) sms = v;
+  } else {
+    cudaGetLastError();
+  }
+  std::string s;
+  TRY(describe(p, args, nargs, c, sms, &s));
+  if (needed) *needed = (int64_t)s.size() + 1;
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>((size_t)cap - 1, s.size());
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return MRW_OK;
+}
+
+mrw_status mrw_features(mrw_node_t root, const mrw_buffer *args, int32_t nargs, float *feat16) {
+  if (!feat16) return fail(MRW_ERR_INVALID_ARG, "feat16 is NULL");
+  Program p;
+  TRY(get_program(root, &p));
+  return features_of(p, args, nargs, feat16);
+}
+
+mrw_status mrw_tune_candidates(mrw_node_t root, const mrw_buffer *args, int32_t nargs, mrw_config *cfgs, int32_t cap,
+                               int32_t *count) {
+  (void)args;
+  (void)nargs;
+  if (!count) return fail(MRW_ERR_INVALID_ARG, "count is NULL");
+  Program p;
+  TRY(get_program(root, &p));
+  const std::vector<mrw_config> v = candidates_for(p.fam);
+  *count = (int32_t)v.size();
+  if (cfgs)
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) cfgs[i] = v[i];
+  return MRW_OK;
+}
+
+mrw_status mrw_tune_measure(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfgs,
+                            int32_t ncfg, int32_t reps, void *stream, float *times_ms) {
+  if (!cfgs || !times_ms || ncfg < 0 || reps < 1 || reps > 1000) return fail(MRW_ERR_INVALID_ARG, "bad arguments");
+  Program p;
+  TRY(get_program(root, &p));
+  for (int i = 0; i < nargs; ++i)
+    if (args[i].memory != MRW_MEM_DEVICE) return fail(MRW_ERR_INVALID_ARG, "the tuner times device buffers");
+  StatusSlot slot;
+  TRY(status_pool().take(&slot));
+  for (int i = 0; i < ncfg; ++i) {
+    float ms = -1.f;
+    const mrw_status s = time_config(p, args, nargs, cfgs[i], reps, stream, slot.dev, &ms);
+    if (s == MRW_ERR_CUDA || s == MRW_ERR_OOM) {
+      status_pool().give(slot);
+      return s;
+    }
+    times_ms[i] = s == MRW_OK ? ms : -1.f;
+  }
+  status_pool().give(slot);
+  return MRW_OK;
+}
+
+mrw_status mrw_tune(mrw_node_t root, const mrw_buffer *args, int32_t nargs, mrw_tune_mode mode, int32_t reps,
+                    void *stream, mrw_config *best, float *best_ms) {
+  Program p;
+  TRY(get_program(root, &p));
+  const std::vector<mrw_config> cands = candidates_for(p.fam);
+  mrw_config pick = default_config(p.fam);
+  float pick_ms = -1.f;
+  if (mode == MRW_TUNE_EXHAUSTIVE) {
+    std::vector<float> t(cands.size());
+    TRY(mrw_tune_measure(root, args, nargs, cands.data(), (int32_t)cands.size(), reps, stream, t.data()));
+    for (size_t i = 0; i < t.size(); ++i)
+      if (t[i] >= 0 && (pick_ms < 0 || t[i] < pick_ms)) {
+        pick_ms = t[i];
+        pick = cands[i];
+      }
+  } else if (mode == MRW_TUNE_PRUNED) {
+    // Algorithm 1's ordered search: fusion modes in order (fused first), then launch shapes in order
+    // of expected benefit; a dimension stops at the first candidate that does not improve the best.
+    for (int f = 0; f < 2; ++f) {
+      float best_f = -1.f;
+      for (int sidx = 0; sidx < 8; ++sidx) {
+        const mrw_config &c = cands[(size_t)(8 * f + sidx)];
+        float ms = -1.f;
+        TRY(mrw_tune_measure(root, args, nargs, &c, 1, reps, stream, &ms));
+        if (ms < 0) continue;
+        const bool improved = best_f < 0 || ms < best_f;
+        if (improved) best_f = ms;
+        if (pick_ms < 0 || ms < pick_ms) {
+          pick_ms = ms;
+          pick = c;
+        }
+        if (!improved) break;  // discard the remaining shapes of this fusion mode
+      }
+      if (f == 0 && best_f >= 0 && pick_ms < best_f) break;
+      if (f == 1 && best_f > pick_ms) break;
+    }
+  } else if (mode == MRW_TUNE_MODEL) {
+    mrw_model *m = nullptr;
+    std::vector<mrw_config> cfgs;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      m = installed_model().model;
+      cfgs = installed_model().cfgs;
+    }
+    if (!m || (int)cfgs.size() != m->d.k) return fail(MRW_ERR_INVALID_ARG, "no cost model installed");
+    float f[MRW_NFEATURES];
+    TRY(features_of(p, args, nargs, f));
+    int b = 0;
+    TRY(model_predict(m, f, &b));
+    pick = cfgs[(size_t)b];
+  } else {
+    return fail(MRW_ERR_INVALID_ARG, "unknown tune mode");
+  }
+  const std::string key = tree_signature(root) + "|" + workload_signature(args, nargs);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    kb()[key] = {pick, pick_ms, (int)mode};
+  }
+  if (best) *best = pick;
+  if (best_ms) *best_ms = pick_ms;
+  return MRW_OK;
+}
+
+mrw_status mrw_kb_save(const char *path) {
+  if (!path) return fail(MRW_ERR_INVALID_ARG, "path is NULL");
+  std::ofstream f(path);
+  if (!f) return fail(MRW_ERR_INVALID_ARG, "cannot write %s", path);
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (const auto &kv : kb()) {
+    const mrw_config &c = kv.second.cfg;
+    f << kv.first << "\t" << c.fusion << " " << c.block << " " << c.ctas_per_sm << " " << c.tile_rows << " "
+      << c.tile_cols << " " << c.unroll << "\t" << kv.second.ms << "\t" << kv.second.source << "\n";
+  }
+  return f ? MRW_OK : fail(MRW_ERR_INVALID_ARG, "write failed: %s", path);
+}
+
+mrw_status mrw_kb_load(const char *path) {
+  if (!path) return fail(MRW_ERR_INVALID_ARG, "path is NULL");
+  std::ifstream f(path);
+  if (!f) return fail(MRW_ERR_INVALID_ARG, "cannot read %s", path);
+  std::string line;
+  std::map<std::string, KbRecord> add;
+  while (std::getline(f, line)) {
+    if (line.empty()) continue;
+    const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 + 1), t3 = line.find('\t', t2 + 1);
+    if (t1 == std::string::npos || t2 == std::string::npos || t3 == std::string::npos)
+      return fail(MRW_ERR_INVALID_ARG, "malformed knowledge-base line");
+    KbRecord r{};
+    std::istringstream cs(line.substr(t1 + 1, t2 - t1 - 1));
+    cs >> r.cfg.fusion >> r.cfg.block >> r.cfg.ctas_per_sm >> r.cfg.tile_rows >> r.cfg.tile_cols >> r.cfg.unroll;
+    if (!cs || check_config(r.cfg) != MRW_OK) return fail(MRW_ERR_INVALID_ARG, "malformed configuration in %s", path);
+    r.ms = std::stof(line.substr(t2 + 1, t3 - t2 - 1));
+    r.source = std::stoi(line.substr(t3 + 1));
+    add[line.substr(0, t1)] = r;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto &kv : add) kb()[kv.first] = kv.second;
+  return MRW_OK;
+}
+
+mrw_status mrw_kb_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  kb().clear();
+  return MRW_OK;
+}
+
+int64_t mrw_kb_size(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return (int64_t)kb().size();
+}
+
+// --------------------------------------------------------------------------------------------
+// Cost model
+// --------------------------------------------------------------------------------------------
+mrw_status mrw_model_create(int32_t k, int32_t hidden, uint64_t seed, mrw_model_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || k > 64 || hidden < 1 || hidden > 128) return fail(MRW_ERR_INVALID_ARG, "K in 1..64, hidden in 1..128");
+  mrw_model *m = new (std::nothrow) mrw_model();
+  if (!m) return fail(MRW_ERR_OOM, "model");
+  m->d = mlp_dims(MRW_NFEATURES, hidden, k);
+  const int64_t np = m->d.nparams;
+  cudaGetDevice(&m->device);
+  cudaError_t e = cudaMalloc(&m->master, sizeof(float) * (size_t)(4 * np + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&m->bf, sizeof(uint16_t) * (size_t)np);
+  if (e != cudaSuccess) {
+    mrw_model_release(m);
+    return cuda_fail(e, "model buffers");
+  }
+  m->m = m->master + np;
+  m->v = m->m + np;
+  m->grads = m->v + np;
+  m->loss = m->grads + np;
+  // He-uniform weights, zero biases
+  std::mt19937_64 rng(seed);
+  std::vector<float> h((size_t)np, 0.f);
+  auto he = [&](int64_t off, int64_t fan_out, int64_t fan_in) {
+    std::uniform_real_distribution<float> u(-std::sqrt(6.f / fan_in), std::sqrt(6.f / fan_in));
+    for (int64_t i = 0; i < fan_out * fan_in; ++i) h[(size_t)(off + i)] = u(rng);
+  };
+  he(m->d.off_w1, hidden, MRW_NFEATURES);
+  he(m->d.off_w2, hidden, hidden);
+  he(m->d.off_w3, k, hidden);
+  const mrw_status s = mrw_model_set_params(m, h.data());
+  if (s != MRW_OK) {
+    mrw_model_release(m);
+    return s;
+  }
+  *out = m;
+  return MRW_OK;
+}
+
+void mrw_model_release(mrw_model_t m) {
+  if (!m) return;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (installed_model().model == m) {
+      installed_model().model = nullptr;
+      installed_model().cfgs.clear();
+    }
+  }
+  if (m->master) cudaFree(m->master);
+  if (m->bf) cudaFree(m->bf);
+  if (m->idx) cudaFree(m->idx);
+  delete m;
+}
+
+int64_t mrw_model_num_params(mrw_model_t m) { return m ? m->d.nparams : 0; }
+
+mrw_status mrw_model_set_params(mrw_model_t m, const float *host_params) {
+  if (!m || !host_params) return fail(MRW_ERR_INVALID_ARG, "NULL argument");
+  const int64_t np = m->d.nparams;
+  CU(cudaMemcpy(m->master, host_params, sizeof(float) * (size_t)np, cudaMemcpyHostToDevice));
+  CU(cudaMemset(m->m, 0, sizeof(float) * (size_t)(3 * np + 1)));
+  CU(launch_mlp_round_bf16(m->master, m->bf, np, nullptr));
+  CU(cudaDeviceSynchronize());
+  m->step = 0;
+  return MRW_OK;
+}
+
+mrw_status mrw_model_get_params(mrw_model_t m, float *host_params) {
+  if (!m || !host_params) return fail(MRW_ERR_INVALID_ARG, "NULL argument");
+  CU(cudaMemcpy(host_params, m->master, sizeof(float) * (size_t)m->d.nparams, cudaMemcpyDeviceToHost));
+  return MRW_OK;
+}
+
+mrw_status mrw_model_forward(mrw_model_t m, const float *x, int64_t n, float *y, void *stream) {
+  if (!m || (n > 0 && (!x || !y)) || n < 0) return fail(MRW_ERR_INVALID_ARG, "bad arguments");
+  CU(launch_mlp_forward(m->d, m->bf, x, n, y, (cudaStream_t)stream));
+  return MRW_OK;
+}
+
+mrw_status mrw_model_gradients(mrw_model_t m, const float *x, const float *t, int64_t n, float *grads, float *loss,
+                               void *stream) {
+  if (!m || !x || !t || !grads || n < 1) return fail(MRW_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaMemsetAsync(grads, 0, sizeof(float) * (size_t)m->d.nparams, s));
+  CU(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+  CU(launch_mlp_backward(m->d, m->bf, x, t, nullptr, n, 1.f / (float)(n * m->d.k), grads, m->loss, s));
+  float l = 0;
+  CU(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (loss) *loss = l / (float)(n * m->d.k);
+  return MRW_OK;
+}
+
+mrw_status mrw_model_adam_step(mrw_model_t m, const float *grads, float lr, void *stream) {
+  if (!m || !grads) return fail(MRW_ERR_INVALID_ARG, "bad arguments");
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->step));
+  const float bc2 = (float)(1.0 - std::pow(0.999, (double)m->step));
+  CU(launch_mlp_adam(m->master, m->m, m->v, grads, m->d.nparams, lr, b1, b2, 1e-8f, bc1, bc2, m->bf,
+                     (cudaStream_t)stream));
+  return MRW_OK;
+}
+
+mrw_status mrw_model_train(mrw_model_t m, const float *x, const float *t, int64_t n, int32_t epochs, int32_t batch,
+                           float lr, uint64_t seed, void *stream, float *final_loss) {
+  if (!m || !x || !t || n < 1 || epochs < 0 || batch < 1) return fail(MRW_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->idx_cap < n) {
+    if (m->idx) cudaFree(m->idx);
+    m->idx = nullptr;
+    m->idx_cap = 0;
+    CU(cudaMalloc(&m->idx, sizeof(int32_t) * (size_t)n));
+    m->idx_cap = n;
+  }
+  std::vector<int32_t> order((size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[(size_t)i] = (int32_t)i;
+  std::mt19937_64 rng(seed);
+  float last = 0.f;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    CU(cudaMemcpyAsync(m->idx, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+    for (int64_t b0 = 0; b0 < n; b0 += batch) {
+      const int64_t cnt = std::min<int64_t>(batch, n - b0);
+      CU(cudaMemsetAsync(m->grads, 0, sizeof(float) * (size_t)m->d.nparams, s));
+      CU(launch_mlp_backward(m->d, m->bf, x, t, m->idx + b0, cnt, 1.f / (float)(cnt * m->d.k), m->grads, m->loss, s));
+      TRY(mrw_model_adam_step(m, m->grads, lr, s));
+    }
+    float l = 0;
+    CU(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));  // `order` is reshuffled next epoch
+    last = l / (float)(n * m->d.k);
+  }
+  if (final_loss) *final_loss = last;
+  return MRW_OK;
+}
+
+mrw_status mrw_tune_set_model(mrw_model_t m, const mrw_config *cfgs, int32_t k) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!m) {
+    installed_model().model = nullptr;
+    installed_model().cfgs.clear();
+    return MRW_OK;
+  }
+  if (!cfgs || k != m->d.k) return fail(MRW_ERR_INVALID_ARG, "the model needs one configuration per output");
+  for (int i = 0; i < k; ++i) TRY(check_config(cfgs[i]));
+  installed_model().model = m;
+  installed_model().cfgs.assign(cfgs, cfgs + k);
+  return MRW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal interface between the host runtime (mrw_host.cpp) and the CUDA kernels.
+// Not part of the public ABI (include/mrw.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mrw {
+
+// ------------------------------------------------------------------------------------------
+// Image stages, as seen by the fused kernels
+// ------------------------------------------------------------------------------------------
+enum OpKind : int32_t { OP_NOISE = 0, OP_SOLARISE = 1, OP_MIRROR = 2, OP_BLUR = 3, OP_THRESH = 4 };
+enum RedKind : int32_t { RED_NONE = 0, RED_COUNT3 = 1, RED_SUM = 2 };
+
+constexpr int kMaxChainOps = 16;     // pointwise ops fused into one kernel
+constexpr int kMaxNoisePerGroup = 2; // noise ops whose column hashes stay in registers
+
+// One pointwise op of a fused chain.
+//   seed  : OP_NOISE seed (the kernels apply F = MurmurHash3 fmix32 to it, after XOR-ing in the
+//           batched instance's seed in the stencil kernel)
+//   flip  : the op's column coordinate is W-1-x (1) or x (0), x being the group's anchor column
+//           (the output column for a chain; the blur's input column for a stencil prefix;
+//           the output column for a stencil suffix)
+//   t     : OP_THRESH thresholds, t0 | t1 << 8
+struct ChainOp {
+  int32_t kind;
+  uint32_t seed;
+  int32_t flip;
+  uint32_t t;
+};
+
+// Fused pointwise chain over one u8 image or volume (rows of W pixels).
+struct ChainArgs {
+  const uint8_t *in;
+  uint8_t *out;            // nullptr: reduce only
+  int64_t in_pitch, out_pitch;
+  int64_t rows;            // total rows (D * H)
+  int64_t rows_parallel;   // rows a wave of threads covers; a thread steps rows by this
+  int32_t W;
+  int32_t col_vecs;        // ceil(W / 16)
+  int32_t nops;
+  int32_t mirror;          // parity of mirror ops in the chain: source column = W-1-x
+  int32_t reduce;          // RedKind
+  int32_t pad_;
+  unsigned long long *red; // RED_COUNT3: [3] counts; RED_SUM: [1]
+  ChainOp ops[kMaxChainOps];
+};
+
+// n_noise: number of OP_NOISE entries (<= kMaxNoisePerGroup); unroll in {1, 2, 4, 8}.
+cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Stencil (5x5 box blur) groups and batched instances, TMA-staged tiles
+// ------------------------------------------------------------------------------------------
+struct StencilInstance {
+  int64_t in_off, out_off;  // byte offsets from the arena bases
+  int32_t W, H, D;          // plane width/height, planes
+  int32_t pitch_in, pitch_out;
+  uint32_t seed_xor;        // XOR-ed into every noise op's seed (batched instance seed)
+  int64_t tile_base;        // first global tile index of this instance
+  int32_t tiles_x, tiles_y;
+};
+
+struct StencilArgs {
+  const CUtensorMap *maps;          // one 3-D map {W, H, D} per instance, device memory
+  const StencilInstance *inst;      // device memory
+  const int64_t *tile_prefix;       // [ninst + 1] device memory
+  const uint8_t *in_base;
+  uint8_t *out_base;
+  unsigned int *queue;              // tile counter, zeroed before the launch
+  unsigned int *status;             // device status word (bounded waits)
+  int64_t total_tiles;
+  int32_t ninst;
+  int32_t halo;                     // 2 with a blur, 0 for a pointwise-only group
+  int32_t tile_h, tile_w;           // output tile (tile_w multiple of 16)
+  int32_t box_w, box_h;             // TMA box
+  int32_t npre, nsuf;               // prefix ops (before the blur) and suffix ops
+  int32_t mpre, msuf;               // mirror parity of prefix and suffix
+  int32_t reduce;                   // reserved (0)
+  uint32_t wait_polls;              // 0: default bound; N > 0: give up a tile wait after N - 1 polls
+                                    // (failure-detection tests set it through MRW_TEST_WAIT_POLLS)
+  ChainOp pre[kMaxChainOps];
+  ChainOp suf[kMaxChainOps];
+};
+
+// Shared-memory bytes the stencil kernel needs for a tile shape.
+size_t stencil_smem_bytes(int tile_h, int tile_w, int halo);
+cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+// Set the kernel's shared-memory limit; call once before capturing a launch into a graph.
+cudaError_t stencil_prepare();
+// Encode a 3-D u8 tensor map for `base` with the stencil box of the given tile shape.
+cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t H, int64_t D, int64_t pitch,
+                          int box_w, int box_h);
+
+// ------------------------------------------------------------------------------------------
+// N-body
+// ------------------------------------------------------------------------------------------
+struct LoopCtrl {
+  unsigned long long iter;
+  unsigned long long max_iters;
+};
+
+struct NBodyParams {
+  float4 *x, *v, *a;
+  int32_t n;
+  float G, eps2, dt;
+};
+
+// a = G sum_j ... ; with kick: v += dt/2 a. bodies_per_thread in {1, 2, 4}.
+cudaError_t launch_nbody_force(const NBodyParams &p, int kick, int bodies_per_thread, int grid, int block,
+                               cudaStream_t s);
+cudaError_t launch_nbody_drift(const NBodyParams &p, cudaStream_t s);
+cudaError_t launch_nbody_kick(const NBodyParams &p, cudaStream_t s);
+// Build and instantiate the device-controlled Loop graph: ctrl->iter = 0, then a conditional
+// WHILE node whose body is {drift (advances the counter, sets the condition), force + kick}.
+cudaError_t build_nbody_loop_graph(const NBodyParams &p, LoopCtrl *ctrl, int64_t iters, int bodies_per_thread,
+                                   int grid, int block, cudaGraphExec_t *exec);
+
+// ------------------------------------------------------------------------------------------
+// SAXPY and helpers
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_saxpy(const float *x, float *y, int64_t n, float alpha, int grid, int block, cudaStream_t s);
+cudaError_t launch_fill_u32(unsigned int *p, unsigned int v, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Cost-model MLP (bf16 weights, fp32 accumulation)
+// ------------------------------------------------------------------------------------------
+struct MlpDims {
+  int32_t nin, hidden, k;
+  int64_t off_w1, off_b1, off_w2, off_b2, off_w3, off_b3, nparams;
+};
+MlpDims mlp_dims(int nin, int hidden, int k);
+cudaError_t launch_mlp_round_bf16(const float *master, uint16_t *bf, int64_t n, cudaStream_t s);
+cudaError_t launch_mlp_forward(const MlpDims &d, const uint16_t *wbf, const float *x, int64_t n, float *y,
+                               cudaStream_t s);
+// grads must be zeroed by the caller; loss_acc (device float) accumulates sum of squared errors.
+cudaError_t launch_mlp_backward(const MlpDims &d, const uint16_t *wbf, const float *x, const float *t,
+                                const int32_t *idx, int64_t n, float scale, float *grads, float *loss_acc,
+                                cudaStream_t s);
+cudaError_t launch_mlp_adam(float *master, float *m, float *v, const float *g, int64_t n, float lr, float b1,
+                            float b2, float eps, float bc1, float bc2, uint16_t *bf, cudaStream_t s);
+
+}  // namespace mrw

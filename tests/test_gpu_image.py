@@ -1,0 +1,150 @@
+"""GPU parity of the fused pointwise chain (Filter Pipeline, Map / MapReduce segmentation) against
+the CPU oracle: bit-exact for every integer stage."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import build_image_tree, empty_like_device, oracle_tree, round_up, run_image, to_device
+from oracle import image as O
+from oracle import skeleton as S
+from paper_1510_06585_gb300 import inputs
+from paper_1510_06585_gb300 import mrw as M
+
+pytestmark = pytest.mark.gpu
+
+FILTER = ["noise", "solarise", "mirror"]
+
+
+def test_filter_pipeline_1024_fused_and_unfused():
+    img = inputs.filter_image(1024, 1024)
+    want = O.filter_pipeline(img, inputs.SEED_NOISE)
+    tree = build_image_tree(FILTER, {0: inputs.SEED_NOISE})
+    for cfg in (None, M.config(), M.config(fusion=M.MRW_FUSE_NONE)):
+        got, _ = run_image(tree, img, cfg)
+        assert np.array_equal(got, want)
+
+
+def test_filter_pipeline_odd_widths_and_8x8_brute_force():
+    tree = build_image_tree(FILTER, {0: 2})
+    for (h, w) in [(8, 8), (1, 1), (3, 7)] + [(5, k) for k in range(1, 34)] + [(7, 1000), (2, 1023), (3, 4097)]:
+        img = inputs.filter_image(h, w, seed=1000 + w)
+        got, _ = run_image(tree, img)
+        assert np.array_equal(got, O.filter_pipeline(img, 2)), (h, w)
+
+
+def test_padded_pitches():
+    tree = build_image_tree(FILTER, {0: 9})
+    for (h, w, pitch) in [(9, 17, 48), (4, 100, 256), (6, 16, 16), (3, 31, 4096)]:
+        img = inputs.filter_image(h, w, seed=w)
+        got, _ = run_image(tree, img, pitch=pitch)
+        assert np.array_equal(got, O.filter_pipeline(img, 9)), (h, w, pitch)
+
+
+def test_output_padding_bytes_are_not_written():
+    img = inputs.filter_image(10, 21)
+    x = to_device(img, 64)
+    y = empty_like_device(img, 64, fill=0xAB)
+    M.execute(build_image_tree(FILTER, {0: 2}), [x, y]).wait(60000)
+    store = y.as_strided((10, 64), (64, 1)).cpu().numpy()
+    assert (store[:, 21:] == 0xAB).all()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_chains_match_depth_first_oracle(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names = [("noise", "solarise", "mirror", "threshold3")[int(k)] for k in rng.integers(0, 4, size=int(rng.integers(1, 9)))]
+    seeds = {i: int(rng.integers(0, 2 ** 32)) for i in range(len(names))}
+    h, w = int(rng.integers(1, 40)), int(rng.integers(1, 300))
+    img = inputs.filter_image(h, w, seed=seed)
+    want, _ = S.evaluate_image(oracle_tree(names, seeds), img)
+    tree = build_image_tree(names, seeds)
+    for cfg in (M.config(), M.config(fusion=M.MRW_FUSE_NONE), M.config(block=128, ctas_per_sm=2, unroll=1)):
+        got, _ = run_image(tree, img, cfg)
+        assert np.array_equal(got, want), (names, h, w)
+
+
+def test_every_candidate_config_gives_the_same_bytes():
+    img = inputs.filter_image(333, 517, seed=5)
+    tree = build_image_tree(["noise", "mirror", "solarise", "noise"], {0: 3, 3: 4})
+    want, _ = S.evaluate_image(oracle_tree(["noise", "mirror", "solarise", "noise"], {0: 3, 3: 4}), img)
+    for c in M.tune_candidates(tree, [img, img]):
+        got, _ = run_image(tree, img, c)
+        assert np.array_equal(got, want), c.as_tuple()
+
+
+def test_volume_rows_are_counted_across_planes():
+    vol = inputs.volume(3, 5, 40, seed=2)
+    tree = M.map_(build_image_tree(["noise", "mirror"], {0: 77}))
+    got, _ = run_image(tree, vol)
+    assert np.array_equal(got, O.mirror(O.noise(vol, 77)))
+
+
+def test_segmentation_small_volumes():
+    for (d, h, w) in [(1, 1, 1), (2, 3, 17), (8, 64, 100), (4, 33, 512)]:
+        vol = inputs.volume(d, h, w, seed=d * w)
+        tree = M.mapreduce(M.map_(M.stage("threshold3")))
+        labels_w, counts_w = O.segmentation(vol)
+        for cfg in (M.config(), M.config(fusion=M.MRW_FUSE_NONE)):
+            labels, counts = run_image(tree, vol, cfg, reduce_k=3)
+            assert np.array_equal(labels, labels_w) and np.array_equal(counts, counts_w), (d, h, w)
+
+
+def test_segmentation_512_cubed_full_size():
+    vol = inputs.volume(512, 512, 512)
+    tree = M.mapreduce(M.map_(M.stage("threshold3")))
+    labels, counts = run_image(tree, vol, None, reduce_k=3)
+    hist, _ = np.histogram(vol, bins=[0, 85, 170, 256])
+    assert np.array_equal(counts, hist.astype(np.int64))
+    assert counts.sum() == 512 ** 3
+    # labels: compare plane chunks against the oracle stage
+    for z in range(0, 512, 64):
+        assert np.array_equal(labels[z:z + 64], O.threshold3(vol[z:z + 64])), z
+
+
+def test_mapreduce_sum_of_a_noisy_chain():
+    img = inputs.filter_image(77, 301, seed=3)
+    names = ["noise", "solarise"]
+    tree = M.mapreduce(M.map_(build_image_tree(names, {0: 5})))
+    out, red = run_image(tree, img, reduce_k=1)
+    want, total = S.evaluate_image(("mapreduce", oracle_tree(names, {0: 5}), "add"), img)
+    assert np.array_equal(out, want) and red[0] == total[0]
+
+
+def test_loop_of_a_chain():
+    img = inputs.filter_image(19, 45, seed=4)
+    body = build_image_tree(FILTER, {0: 8})
+    got, _ = run_image(M.loop(body, 3), img)
+    want, _ = S.evaluate_image(("loop", oracle_tree(FILTER, {0: 8}), 3), img)
+    assert np.array_equal(got, want)
+
+
+def test_host_buffers_are_staged():
+    img = inputs.filter_image(200, 301, seed=6)
+    out = np.zeros_like(img)
+    tree = build_image_tree(FILTER, {0: 2})
+    M.execute(tree, [img, out]).wait(60000)
+    assert np.array_equal(out, O.filter_pipeline(img, 2))
+    pinned_in = torch.from_numpy(img).pin_memory()
+    pinned_out = torch.zeros_like(pinned_in).pin_memory()
+    counts = torch.zeros(3, dtype=torch.int64).pin_memory()
+    seg = M.mapreduce(M.map_(M.stage("threshold3")))
+    M.execute(seg, [pinned_in, pinned_out, counts]).wait(60000)
+    labels_w, counts_w = O.segmentation(img)
+    assert np.array_equal(pinned_out.numpy(), labels_w) and np.array_equal(counts.numpy(), counts_w)
+
+
+def test_in_place_pointwise_chain():
+    img = inputs.filter_image(64, 256, seed=7)
+    x = to_device(img)
+    M.execute(build_image_tree(["noise", "solarise"], {0: 1}), [x, x]).wait(60000)
+    assert np.array_equal(x.cpu().numpy(), O.solarise(O.noise(img, 1)))
+    with pytest.raises(M.MrwError):
+        M.execute(build_image_tree(FILTER, {0: 1}), [x, x])
+
+
+def test_future_elapsed_and_query():
+    img = inputs.filter_image(512, 512)
+    f = M.execute(build_image_tree(FILTER, {0: 2}), [to_device(img), empty_like_device(img)])
+    f.wait(60000)
+    assert f.elapsed_ms() > 0
+    assert M.load().mrw_future_query(f.h) == M.MRW_OK
