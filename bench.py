@@ -198,6 +198,23 @@ def run_mrw(args):
     peaks, peak_src = load_peaks()
     K, W = args.steps, args.warmup
 
+    if not args.segmentation:  # profiling runs of one extra workload only
+        lib = M.load()
+        pending = []
+
+        def drain_only():
+            for fut in pending:
+                s = lib.mrw_future_wait(fut, -1)
+                lib.mrw_future_release(fut)
+                M.check(s, "future")
+            pending.clear()
+
+        out = extras(M, lib, device, world, torch.cuda.current_stream().cuda_stream, peaks, pending, drain_only,
+                     set(args.workloads.split(",")), args.batch_n)
+        if rank == 0:
+            print(json.dumps({"workloads": out}), flush=True)
+        return
+
     # ---------------- headline: fused Map + MapReduce segmentation ----------------
     vol = inputs.volume(*SEG_SHAPE)
     sets = []
@@ -282,7 +299,8 @@ def run_mrw(args):
 
     # ---------------- other workloads of the hot path ----------------
     if args.extras:
-        result["workloads"] = extras(M, lib, device, world, stream, peaks, pending, drain)
+        result["workloads"] = extras(M, lib, device, world, stream, peaks, pending, drain,
+                                     set(args.workloads.split(",")), args.batch_n)
 
     # ---------------- CPU baseline (oracle) ----------------
     if rank == 0 and world == 1:
@@ -294,7 +312,7 @@ def run_mrw(args):
         dist.destroy_process_group()
 
 
-def extras(M, lib, device, world, stream, peaks, pending, drain):
+def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n):
     import torch
 
     from paper_1510_06585_gb300 import inputs
@@ -325,7 +343,7 @@ def extras(M, lib, device, world, stream, peaks, pending, drain):
     fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
     # Filter Pipeline (noise -> solarise -> mirror)
     ftree = M.pipeline(M.stage("noise", seed=2), M.stage("solarise"), M.stage("mirror"))
-    for side, nsets in ((1024, 1), (8192, 2)):
+    for side, nsets in (((1024, 1), (8192, 2)) if "filter" in which else ()):
         img = inputs.filter_image(side, side)
         sets = []
         for _ in range(nsets):
@@ -339,6 +357,18 @@ def extras(M, lib, device, world, stream, peaks, pending, drain):
                                  "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
                                  "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
                                  "l2": "resident (2 MiB)" if side == 1024 else "2 rotating sets, 256 MiB"}
+    if "nbody" in which:
+        out.update(nbody_workload(M, device, timed, launcher, fused, unfused))
+    if "batched" in which:
+        out.update(batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n))
+    return out
+
+
+def nbody_workload(M, device, timed, launcher, fused, unfused):
+    import torch
+
+    from paper_1510_06585_gb300 import inputs
+    out = {}
     # N-body: accel + Loop(100 KDK)
     n = 65536
     xs, vs, as_ = inputs.nbody(n)
@@ -356,8 +386,16 @@ def extras(M, lib, device, world, stream, peaks, pending, drain):
                               "frac_alu": round(gf / alu_peak, 4), "alu_peak_gflops": round(alu_peak, 1),
                               "kernel_per_step_host_loop_ms": round(tnu * 1e3, 2),
                               "speedup_fused": round(tnu / tn, 3)}
-    # Batched: 4096 instances of Filter Pipeline + 5x5 blur
-    shapes = inputs.batch_shapes(4096)
+    return out
+
+
+def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n):
+    import torch
+
+    from paper_1510_06585_gb300 import inputs
+    out = {}
+    # Batched: instances of Filter Pipeline + 5x5 blur, sides log-uniform in 64..2048
+    shapes = inputs.batch_shapes(batch_n)
     desc, nbytes = inputs.batch_descriptors(shapes)
     arena = inputs.batch_arena(desc, nbytes)
     bx = torch.from_numpy(arena).to(device)
@@ -377,7 +415,7 @@ def extras(M, lib, device, world, stream, peaks, pending, drain):
     px = float((shapes[:, 0] * shapes[:, 1]).sum())
     tb = timed(blaunch(fused), 5)
     tbu = timed(blaunch(unfused), 3)
-    out["batched_4096"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
+    out[f"batched_{batch_n}"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
                            "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
                            "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
                            "launches_per_step": 1}
@@ -433,6 +471,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrw", choices=["mrw", "reference"])
     ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--workloads", default="filter,nbody,batched",
+                    help="comma list of the extra workloads to run (filter, nbody, batched)")
+    ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
+    ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
+                    help="skip the headline timing (profiling runs of one extra workload)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mrw":
         args.warmup = 3

@@ -150,7 +150,8 @@ typedef struct mrw_config {
   int32_t block;       /* threads per CTA (multiple of 32, 32..1024); 0 = default                */
   int32_t ctas_per_sm; /* resident CTAs per SM the grid is sized for; 0 = default                */
   int32_t tile_rows;   /* image: rows per CTA tile (stencil) ; N-body: bodies per thread (1,2,4) */
-  int32_t tile_cols;   /* image: columns per CTA tile (stencil, multiple of 16)                  */
+  int32_t tile_cols;   /* image: columns per CTA tile (stencil, multiple of 16, <= 256; a blur
+                          tile is capped at 224 so its TMA box with halo fits 256 bytes)        */
   int32_t unroll;      /* image: 16-byte vectors each thread keeps in flight (1, 2, 4, 8)        */
   int32_t reserved[2]; /* must be 0                                                              */
 } mrw_config;
@@ -212,8 +213,10 @@ mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, c
  * instance i reads in_arena + desc[5i] and writes out_arena + desc[5i] with
  * desc[5i .. 5i+4] = {byte offset, W, H, pitch, noise seed}. Both arenas are device memory;
  * offsets must be multiples of 16, pitch a multiple of 16 and >= W, and every instance must lie
- * inside `arena_bytes`. The noise stages of instance i use that instance's seed.
- * `desc` is a host array that is read before the call returns. */
+ * inside `arena_bytes`. Instance i's noise stages use (stage seed XOR desc seed of i), so a tree
+ * built with seed 0 uses each instance's own seed. `desc` is a host array read before the call
+ * returns; the launch (tensor maps, tile tables, graph) is cached per (tree, arenas, desc, cfg,
+ * stream), so calls sharing a cache entry run in stream order. */
 mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t *out_arena, int64_t arena_bytes,
                                const int64_t *desc, int64_t n, const mrw_config *cfg, void *stream,
                                mrw_future_t *out);

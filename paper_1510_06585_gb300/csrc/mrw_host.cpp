@@ -408,7 +408,7 @@ mrw_status check_config(const mrw_config &c) {
   if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return fail(MRW_ERR_INVALID_ARG, "bad ctas_per_sm");
   if (c.unroll && c.unroll != 1 && c.unroll != 2 && c.unroll != 4 && c.unroll != 8)
     return fail(MRW_ERR_INVALID_ARG, "unroll must be 1, 2, 4 or 8");
-  if (c.tile_rows < 0 || c.tile_rows > 252 || c.tile_cols < 0 || c.tile_cols > 224 || c.tile_cols % 16)
+  if (c.tile_rows < 0 || c.tile_rows > 252 || c.tile_cols < 0 || c.tile_cols > 256 || c.tile_cols % 16)
     return fail(MRW_ERR_INVALID_ARG, "bad tile shape");
   if (c.reserved[0] || c.reserved[1]) return fail(MRW_ERR_INVALID_ARG, "reserved config fields must be 0");
   return MRW_OK;
