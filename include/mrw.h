@@ -221,6 +221,31 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
                                const int64_t *desc, int64_t n, const mrw_config *cfg, void *stream,
                                mrw_future_t *out);
 
+/* Allocation-free batched execution. The paper has no counterpart to this call; it serves callers
+ * that must not allocate device memory — a host framework whose device memory belongs to its own
+ * pool allocator, or a latency-critical loop in which cudaMalloc / cudaFree would synchronise the
+ * device. It runs the same persistent stencil kernel as mrw_execute_batched, with the same
+ * arguments and results, but allocates nothing: the kernel's scratch (tile counter, status word,
+ * one tensor map and instance record per instance, tile prefix sum) lives in a file-scope device
+ * array of about 51 KB sized for MRW_NOALLOC_MAX_INSTANCES instances, which every GPU that loads
+ * the library holds until the process exits.
+ *   - n must be 1..MRW_NOALLOC_MAX_INSTANCES; larger batches are rejected with
+ *     MRW_ERR_INVALID_ARG ("takes 1 to 256 instances");
+ *   - the tree must fuse into one kernel: image stages with at most one blur and at most 16
+ *     pointwise stages on each side of it, cfg->fusion == MRW_FUSE_ALL (else MRW_ERR_UNSUPPORTED);
+ *   - the call enqueues on `stream` and returns; it creates no future: synchronise the stream to
+ *     wait. A tile wait that gives up its bound leaves that tile unwritten and records the
+ *     failure only inside the array;
+ *   - every call reuses the one array, clearing its counter and status word on entry: calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on it and must be
+ *     serialised by the caller;
+ *   - the first call on each device looks up the array's device address with that device current;
+ *     make that first call before any stream capture on that device. */
+#define MRW_NOALLOC_MAX_INSTANCES 256
+mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t *in_arena, uint8_t *out_arena,
+                                       int64_t arena_bytes, const int64_t *desc, int64_t n, const mrw_config *cfg,
+                                       void *stream);
+
 /* Wait for a future: MRW_OK when the work finished, MRW_ERR_TIMEOUT if `timeout_ms` (< 0 =
  * forever) passed first (the future stays valid), MRW_ERR_DEVICE if a kernel gave up a bounded
  * wait, MRW_ERR_CUDA if the stream reported an error. */

@@ -18,6 +18,8 @@
 // Waits: only thread 0 waits on a TMA mbarrier, for a bounded number of polls; if the bound is
 // reached it records MRW status word 1 and the whole CTA leaves after a second bounded wait for
 // its copies in flight.
+#include <mutex>
+
 #include "mrw_internal.h"
 
 namespace mrw {
@@ -383,6 +385,108 @@ cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free batched launch
+//
+// Some callers cannot allocate device memory (for example a host framework whose device memory is
+// owned by its own pool allocator, or a loop that must not call cudaMalloc / cudaFree because those
+// calls synchronise the device). For them the per-launch scratch of the stencil kernel — the tile
+// counter, the status word, one tensor map and one instance record per instance, and the tile
+// prefix sum — lives in the file-scope device array below, sized for kNoAllocMaxInstances
+// instances (about 51 KB, held by every GPU that loads the library until the process exits).
+// Every call reuses the same array: the counter and status word are cleared on each call, and two
+// calls whose work overlaps on the GPU race on the array.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct NoAllocTables {
+  CUtensorMap maps[kNoAllocMaxInstances];
+  StencilInstance inst[kNoAllocMaxInstances];
+  int64_t prefix[kNoAllocMaxInstances + 1];
+  unsigned int queue;
+  unsigned int status;
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocTables)];
+
+// Host staging copy of the tables (a static object: building them allocates nothing). The copies
+// from it are made from pageable memory, so each call's copy has left it when the call returns.
+static NoAllocTables g_noalloc_host;
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch for the current device, looked up once per device with
+// that device current (host code cannot use the symbol itself as a device address).
+cudaError_t noalloc_scratch_ptr(NoAllocTables **out) {
+  static NoAllocTables *ptrs[256] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    ptrs[dev] = reinterpret_cast<NoAllocTables *>(p);
+  }
+  *out = ptrs[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t stencil_noalloc_scratch_bytes() { return sizeof(NoAllocTables); }
+
+cudaError_t launch_stencil_noalloc(StencilArgs a, const uint8_t *in_base, uint8_t *out_base, const int64_t *desc,
+                                   int64_t n, int sms, int cps, size_t smem, cudaStream_t s) {
+  if (n < 1 || n > kNoAllocMaxInstances) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocTables *dev = nullptr;
+  cudaError_t e = noalloc_scratch_ptr(&dev);
+  if (e != cudaSuccess) return e;
+  e = stencil_prepare();
+  if (e != cudaSuccess) return e;
+  NoAllocTables &h = g_noalloc_host;
+  int64_t tiles = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
+    e = encode_u8_map(&h.maps[i], in_base + off, W, H, 1, pitch, a.box_w, a.box_h);
+    if (e != cudaSuccess) return e;
+    StencilInstance &in = h.inst[i];
+    in.in_off = off;
+    in.out_off = off;
+    in.W = (int32_t)W;
+    in.H = (int32_t)H;
+    in.D = 1;
+    in.pitch_in = in.pitch_out = (int32_t)pitch;
+    in.seed_xor = (uint32_t)desc[5 * i + 4];
+    in.tiles_x = (int32_t)((W + a.tile_w - 1) / a.tile_w);
+    in.tiles_y = (int32_t)((H + a.tile_h - 1) / a.tile_h);
+    in.tile_base = tiles;
+    h.prefix[i] = tiles;
+    tiles += (int64_t)in.tiles_x * in.tiles_y;
+  }
+  h.prefix[n] = tiles;
+  if (tiles >= (int64_t)UINT32_MAX - 1) return cudaErrorInvalidValue;
+  e = cudaMemcpyAsync(dev->maps, h.maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev->inst, h.inst, sizeof(StencilInstance) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev->prefix, h.prefix, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&dev->queue, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  a.maps = dev->maps;
+  a.inst = dev->inst;
+  a.tile_prefix = dev->prefix;
+  a.in_base = in_base;
+  a.out_base = out_base;
+  a.queue = &dev->queue;
+  a.status = &dev->status;
+  a.total_tiles = tiles;
+  a.ninst = (int32_t)n;
+  const int64_t grid = tiles < (int64_t)sms * cps ? tiles : (int64_t)sms * cps;
+  return launch_stencil(a, (int)(grid > 0 ? grid : 1), kBlock, smem, s);
 }
 
 }  // namespace mrw

@@ -2126,3 +2126,113 @@ mrw_status mrw_tune_set_model(mrw_model_t m, const mrw_config *cfgs, int32_t k) 
 }
 
 }  // extern "C"
+
+// ============================================================================================
+// Allocation-free batched execution
+// ============================================================================================
+namespace {
+
+// Image stages of a tree, depth first, into a fixed array (no heap allocation).
+mrw_status collect_image_stages(const mrw_node *n, ImgStage *out, int *cnt, int cap, int depth) {
+  if (depth > 64) return fail(MRW_ERR_UNSUPPORTED, "tree deeper than 64 levels");
+  switch (n->kind) {
+    case N_STAGE: {
+      const int ok = op_kind_of(n->stage);
+      if (ok < 0) return fail(MRW_ERR_UNSUPPORTED, "the allocation-free batched call runs image stages only");
+      if (*cnt >= cap) return fail(MRW_ERR_UNSUPPORTED, "more than %d image stages", cap);
+      const mrw_stage_params &q = n->params;
+      if (n->stage == MRW_ST_THRESHOLD3 && (q.t0 < 0 || q.t0 > 255 || q.t1 < 0 || q.t1 > 255))
+        return fail(MRW_ERR_INVALID_ARG, "threshold outside [0, 255]");
+      out[(*cnt)++] = {ok, q.seed, (uint32_t)(q.t0 & 0xFF) | ((uint32_t)(q.t1 & 0xFF) << 8), q.nu, q.wg};
+      return MRW_OK;
+    }
+    case N_PIPELINE:
+      if (n->kids.empty()) return fail(MRW_ERR_INVALID_ARG, "empty pipeline");
+      for (const mrw_node *c : n->kids) TRY(collect_image_stages(c, out, cnt, cap, depth + 1));
+      return MRW_OK;
+    case N_MAP:
+      return collect_image_stages(n->kids[0], out, cnt, cap, depth + 1);
+    case N_LOOP:
+      if (n->loop.kind != MRW_LOOP_FOR) return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", n->loop.kind);
+      for (int64_t i = 0; i < n->loop.max_iters; ++i) TRY(collect_image_stages(n->kids[0], out, cnt, cap, depth + 1));
+      return MRW_OK;
+    case N_MAPREDUCE:
+      return fail(MRW_ERR_UNSUPPORTED, "batched MapReduce");
+  }
+  return fail(MRW_ERR_INVALID_ARG, "bad node");
+}
+
+void fill_ops_array(const ImgStage *v, int n, ChainOp *ops, int *parity) {
+  int m = 0;
+  for (int i = 0; i < n; ++i) m ^= (v[i].kind == OP_MIRROR);
+  int before = 0;
+  for (int i = 0; i < n; ++i) {
+    ops[i].kind = v[i].kind;
+    ops[i].seed = v[i].seed;
+    ops[i].t = v[i].t;
+    ops[i].flip = m ^ (before & 1);
+    before += v[i].kind == OP_MIRROR;
+  }
+  *parity = m;
+}
+
+}  // namespace
+
+extern "C" mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t *in_arena, uint8_t *out_arena,
+                                                  int64_t arena_bytes, const int64_t *desc, int64_t n,
+                                                  const mrw_config *cfg, void *stream) {
+  if (!root || !in_arena || !out_arena || !desc || arena_bytes <= 0)
+    return fail(MRW_ERR_INVALID_ARG, "the allocation-free batched call needs a tree, arenas and descriptors");
+  if (n < 1 || n > MRW_NOALLOC_MAX_INSTANCES)
+    return fail(MRW_ERR_INVALID_ARG, "the allocation-free batched call takes 1 to %d instances, got %lld",
+                MRW_NOALLOC_MAX_INSTANCES, (long long)n);
+  if ((uintptr_t)in_arena % 16 || (uintptr_t)out_arena % 16)
+    return fail(MRW_ERR_CONSTRAINT, "arenas must be 16-byte aligned");
+  {
+    const uintptr_t a0 = (uintptr_t)in_arena, b0 = (uintptr_t)out_arena;
+    if (a0 < b0 + arena_bytes && b0 < a0 + arena_bytes) return fail(MRW_ERR_INVALID_ARG, "arenas overlap");
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
+    if (W < 1 || H < 1 || W > (1 << 20) || H > (1 << 20)) return fail(MRW_ERR_SHAPE, "instance %lld: bad size", (long long)i);
+    if (off < 0 || off % 16 || pitch % 16 || pitch < W || pitch > INT32_MAX)
+      return fail(MRW_ERR_CONSTRAINT, "instance %lld: offset and pitch must be multiples of 16, pitch >= W",
+                  (long long)i);
+    if (off + H * pitch > arena_bytes) return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
+  }
+  mrw_config c = cfg ? *cfg : default_config(F_IMAGE);
+  TRY(check_config(c));
+  if (c.fusion != MRW_FUSE_ALL)
+    return fail(MRW_ERR_UNSUPPORTED, "kernel-per-stage execution needs intermediate arenas; use mrw_execute_batched");
+  ImgStage st[MRW_MAX_STAGES];
+  int cnt = 0;
+  TRY(collect_image_stages(root, st, &cnt, MRW_MAX_STAGES, 0));
+  int blur_at = -1;
+  for (int i = 0; i < cnt; ++i) {
+    if (st[i].kind != OP_BLUR) continue;
+    if (blur_at >= 0) return fail(MRW_ERR_UNSUPPORTED, "the allocation-free batched call fuses at most one blur");
+    blur_at = i;
+  }
+  const int npre = blur_at >= 0 ? blur_at : cnt, nsuf = blur_at >= 0 ? cnt - blur_at - 1 : 0;
+  if (npre > kMaxChainOps || nsuf > kMaxChainOps)
+    return fail(MRW_ERR_UNSUPPORTED, "more than %d pointwise stages on one side of the blur", kMaxChainOps);
+  StencilArgs a{};
+  a.wait_polls = test_wait_polls();
+  a.halo = blur_at >= 0 ? 2 : 0;
+  a.npre = npre;
+  a.nsuf = nsuf;
+  fill_ops_array(st, npre, a.pre, &a.mpre);
+  fill_ops_array(st + npre + (blur_at >= 0 ? 1 : 0), nsuf, a.suf, &a.msuf);
+  const StencilShape s = stencil_shape(c, a.halo);
+  a.tile_h = s.tile_h;
+  a.tile_w = s.tile_w;
+  a.box_w = s.box_w;
+  a.box_h = s.box_h;
+  int dev = 0, sms = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const cudaError_t e =
+      launch_stencil_noalloc(a, in_arena, out_arena, desc, n, sms, s.cps, s.smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "allocation-free batched launch");
+  return MRW_OK;
+}

@@ -90,6 +90,14 @@ size_t stencil_smem_bytes(int tile_h, int tile_w, int halo);
 cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s);
 // Set the kernel's shared-memory limit; call once before capturing a launch into a graph.
 cudaError_t stencil_prepare();
+// Allocation-free batched launch: the tile counter, status word, tensor maps and instance tables
+// live in a file-scope device array of k_stencil.cu (up to kNoAllocMaxInstances instances).
+// `a` carries the ops and tile shape; the tables are built here from `desc` (n rows of
+// {offset, W, H, pitch, seed}). Returns cudaErrorInvalidValue if n is out of range.
+constexpr int kNoAllocMaxInstances = 256;
+size_t stencil_noalloc_scratch_bytes();
+cudaError_t launch_stencil_noalloc(StencilArgs a, const uint8_t *in_base, uint8_t *out_base, const int64_t *desc,
+                                   int64_t n, int sms, int cps, size_t smem, cudaStream_t s);
 // Encode a 3-D u8 tensor map for `base` with the stencil box of the given tile shape.
 cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t H, int64_t D, int64_t pitch,
                           int box_w, int box_h);

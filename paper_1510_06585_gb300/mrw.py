@@ -25,6 +25,7 @@ MRW_LOOP_FOR = 0
 MRW_FUSE_ALL, MRW_FUSE_NONE = 0, 1
 MRW_TUNE_EXHAUSTIVE, MRW_TUNE_PRUNED, MRW_TUNE_MODEL = 0, 1, 2
 MRW_NFEATURES = 16
+MRW_NOALLOC_MAX_INSTANCES = 256
 
 STAGE_BY_NAME = {"noise": MRW_ST_NOISE_HASH, "solarise": MRW_ST_SOLARISE, "mirror": MRW_ST_MIRROR_H,
                  "blur5": MRW_ST_BOXBLUR5, "threshold3": MRW_ST_THRESHOLD3, "nbody_accel": MRW_ST_NBODY_ACCEL,
@@ -74,6 +75,8 @@ _SIGS = {
                                    ctypes.POINTER(_P)]),
     "mrw_execute_batched": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                            ctypes.POINTER(mrw_config), _P, ctypes.POINTER(_P)]),
+    "mrw_execute_batched_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.c_int64, ctypes.POINTER(mrw_config), _P]),
     "mrw_future_wait": (ctypes.c_int, [_P, ctypes.c_int64]),
     "mrw_future_query": (ctypes.c_int, [_P]),
     "mrw_future_elapsed_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
