@@ -8,9 +8,14 @@
 //
 // Thread -> data: a thread owns one 16-byte column segment (16 pixels) of a row and walks down
 // the rows with stride `rows_parallel`; grid * block is a multiple of the row's segment count so
-// the column stays fixed and the column half of the noise hash is computed once per thread.
-// A mirror stage moves no data: it flips the column coordinate of the stages after it, and the
-// chain reads its source segment reversed (two aligned 16-byte loads and a byte permutation).
+// the column stays fixed: the column half of the noise hash is computed once per thread, and only
+// the thread owning a row's ragged last segment ever masks bytes. A mirror stage moves no data: it
+// flips the column coordinate of the stages after it, and the chain reads its source segment
+// reversed (two aligned 16-byte loads and a byte permutation).
+//
+// Byte arithmetic is SIMD within 32-bit words: solarise flips a byte when its top bit is set; the
+// threshold compares bytes without inter-byte borrows; the class counts accumulate in byte lanes
+// and are folded into 32-bit counters before a lane can overflow.
 //
 // MapReduce (Section 2.1; merging function +, Section 3.4) is fused: per-thread counters, warp
 // reduction with redux.sync, block reduction in shared memory, one 64-bit atomic per block.
@@ -19,8 +24,20 @@
 namespace mrw {
 namespace {
 
+constexpr uint32_t kHi = 0x80808080u;
+constexpr uint32_t kLo7 = 0x7F7F7F7Fu;
+
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// fmix32(v) with its first xor-shift already applied to v (the caller passes v ^ (v >> 16)).
+__device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
   h *= 0x85EBCA6Bu;
   h ^= h >> 13;
   h *= 0xC2B2AE35u;
@@ -62,31 +79,50 @@ __device__ __forceinline__ uint32_t solarise4(uint32_t w) {
   return w ^ (((w >> 7) & 0x01010101u) * 0xFFu);
 }
 
-__device__ __forceinline__ uint32_t thresh4(uint32_t w, uint32_t t) {
-  const uint32_t t0 = (t & 0xFFu) * 0x01010101u, t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
-  return (__vcmpgeu4(w, t0) & 0x01010101u) + (__vcmpgeu4(w, t1) & 0x01010101u);
+// Per byte: 0x80 if a >= t, else 0. Setting a's top bits and clearing t's makes the subtraction
+// borrow-free across bytes; its top bit then compares the low 7 bits, and the top bits of a and t
+// decide the rest. tlo = t & 0x7F7F7F7F.
+__device__ __forceinline__ uint32_t ge4(uint32_t a, uint32_t t, uint32_t tlo) {
+  const uint32_t d = (a | kHi) - tlo;
+  return ((a & ~t) | (~(a ^ t) & d)) & kHi;
 }
 
-__device__ __forceinline__ uint32_t noise_byte(uint32_t p, uint32_t colhash, uint32_t y) {
-  const uint32_t h = fmix32(colhash ^ y);
+struct Thresh {
+  uint32_t t0, t0lo, t1, t1lo;
+};
+
+__device__ __forceinline__ Thresh make_thresh(uint32_t t) {
+  Thresh h;
+  h.t0 = (t & 0xFFu) * 0x01010101u;
+  h.t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
+  h.t0lo = h.t0 & kLo7;
+  h.t1lo = h.t1 & kLo7;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t noise_byte(uint32_t p, uint32_t colpre, uint32_t ypre) {
+  const uint32_t h = fmix32_tail(colpre ^ ypre);
   const int q = (int)p + (int)(h % 41u) - 20;
   return (uint32_t)min(max(q, 0), 255);
 }
 
-__device__ __forceinline__ void noise16(uint32_t (&w)[4], const uint32_t (&ch)[16], uint32_t y) {
+__device__ __forceinline__ void noise16(uint32_t (&w)[4], const uint32_t (&ch)[16], uint32_t ypre) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const uint32_t b0 = noise_byte(w[j] & 0xFFu, ch[4 * j + 0], y);
-    const uint32_t b1 = noise_byte((w[j] >> 8) & 0xFFu, ch[4 * j + 1], y);
-    const uint32_t b2 = noise_byte((w[j] >> 16) & 0xFFu, ch[4 * j + 2], y);
-    const uint32_t b3 = noise_byte(w[j] >> 24, ch[4 * j + 3], y);
+    const uint32_t b0 = noise_byte(w[j] & 0xFFu, ch[4 * j + 0], ypre);
+    const uint32_t b1 = noise_byte((w[j] >> 8) & 0xFFu, ch[4 * j + 1], ypre);
+    const uint32_t b2 = noise_byte((w[j] >> 16) & 0xFFu, ch[4 * j + 2], ypre);
+    const uint32_t b3 = noise_byte(w[j] >> 24, ch[4 * j + 3], ypre);
     w[j] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
   }
 }
 
+// Applies the chain; for a trailing threshold also returns the per-byte ">= t0" / ">= t1" flags
+// (0x01 per byte) so the class counts need no further compares.
 template <int NN>
-__device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (&w)[4], const uint32_t (&ch)[NN > 0 ? NN : 1][16],
-                                            uint32_t y) {
+__device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (&w)[4],
+                                            const uint32_t (&ch)[NN > 0 ? NN : 1][16], uint32_t ypre,
+                                            uint32_t (&g0)[4], uint32_t (&g1)[4]) {
   int kn = 0;
   for (int i = 0; i < a.nops; ++i) {
     const int kind = a.ops[i].kind;
@@ -94,14 +130,18 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (&w)[4]
 #pragma unroll
       for (int j = 0; j < 4; ++j) w[j] = solarise4(w[j]);
     } else if (kind == OP_THRESH) {
-      const uint32_t t = a.ops[i].t;
+      const Thresh t = make_thresh(a.ops[i].t);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = thresh4(w[j], t);
+      for (int j = 0; j < 4; ++j) {
+        g0[j] = ge4(w[j], t.t0, t.t0lo) >> 7;
+        g1[j] = ge4(w[j], t.t1, t.t1lo) >> 7;
+        w[j] = g0[j] + g1[j];
+      }
     } else if (kind == OP_NOISE) {
       if constexpr (NN >= 1) {
-        if (kn == 0) noise16(w, ch[0], y);
+        if (kn == 0) noise16(w, ch[0], ypre);
         if constexpr (NN >= 2) {
-          if (kn == 1) noise16(w, ch[1], y);
+          if (kn == 1) noise16(w, ch[1], ypre);
         }
       }
       ++kn;
@@ -110,11 +150,14 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (&w)[4]
   }
 }
 
+__device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01010101u, 0u); }
+
 template <int NN, bool MIR, int U>
 __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ ChainArgs a) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthreads = a.rows_parallel * a.col_vecs;
-  uint32_t c1 = 0, c2 = 0, cn = 0;
+  // class counts: ge0 = #(label >= 1), ge1 = #(label == 2), n = pixels seen
+  uint32_t cnt_ge0 = 0, cnt_ge1 = 0, cnt_n = 0;
   unsigned long long vsum = 0;
 
   if (gid < nthreads) {
@@ -123,11 +166,13 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
     const int xo = col * 16;
     const int W = a.W;
     const int nv = min(16, W - xo);
+    const bool full = nv == 16;
     const int r = W & 15;
     const int q0 = r >> 2, b = r & 3;
     const uint32_t sel = (uint32_t)(b + 3) | ((uint32_t)(b + 2) << 4) | ((uint32_t)(b + 1) << 8) | ((uint32_t)b << 12);
 
-    // Column half of each noise op's hash, F(F(seed) ^ x), for this thread's 16 columns.
+    // Column half of each noise op's hash, c = F(F(seed) ^ x), stored as c ^ (c >> 16): the first
+    // xor-shift of F(c ^ y) splits into a column part and a row part.
     uint32_t ch[NN > 0 ? NN : 1][16];
     if constexpr (NN > 0) {
       int kn = 0;
@@ -138,7 +183,8 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const uint32_t x = flip ? (uint32_t)(W - 1 - xo - k) : (uint32_t)(xo + k);
-          const uint32_t v = fmix32(fs ^ x);
+          const uint32_t c = fmix32(fs ^ x);
+          const uint32_t v = c ^ (c >> 16);
           if (kn == 0) ch[0][k] = v;
           if constexpr (NN >= 2) {
             if (kn == 1) ch[1][k] = v;
@@ -147,10 +193,16 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
         ++kn;
       }
     }
-    const uint32_t vmask[4] = {nv >= 4 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (1u << (8 * nv)) - 1u),
-                               nv >= 8 ? 0xFFFFFFFFu : (nv <= 4 ? 0u : (1u << (8 * (nv - 4))) - 1u),
-                               nv >= 12 ? 0xFFFFFFFFu : (nv <= 8 ? 0u : (1u << (8 * (nv - 8))) - 1u),
-                               nv >= 16 ? 0xFFFFFFFFu : (nv <= 12 ? 0u : (1u << (8 * (nv - 12))) - 1u)};
+    // valid-byte masks of this thread's segment (all ones unless it is the row's ragged tail)
+    uint32_t vmask[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nb = min(max(nv - 4 * j, 0), 4);
+      vmask[j] = nb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
+    }
+    const bool last_thresh = a.nops > 0 && a.ops[a.nops - 1].kind == OP_THRESH;
+    uint32_t lane0 = 0, lane1 = 0;  // byte-lane counters, folded every 63 segments
+    int since_fold = 0;
     const int64_t step = a.rows_parallel;
     for (int64_t y0 = r0; y0 < a.rows; y0 += U * step) {
       uint4 v[U];
@@ -167,14 +219,35 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
         const int64_t y = y0 + u * step;
         if (y < a.rows) {
           uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-          apply_chain<NN>(a, w, ch, (uint32_t)y);
-          if (a.reduce == RED_COUNT3) {
+          uint32_t g0[4] = {0, 0, 0, 0}, g1[4] = {0, 0, 0, 0};
+          const uint32_t y32 = (uint32_t)(y + a.row0);
+          apply_chain<NN>(a, w, ch, y32 ^ (y32 >> 16), g0, g1);
+          if (a.reduce == RED_COUNT3 && !last_thresh) {
+            // counting labels written by an earlier kernel (kernel-per-stage MapReduce)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              c1 += __popc(w[j] & vmask[j] & 0x01010101u);
-              c2 += __popc(w[j] & vmask[j] & 0x02020202u);
+              g0[j] = ge4(w[j], 0x01010101u, 0x01010101u) >> 7;
+              g1[j] = ge4(w[j], 0x02020202u, 0x02020202u) >> 7;
             }
-            cn += nv;
+          }
+          if (a.reduce == RED_COUNT3) {
+            if (full) {
+              lane0 += (g0[0] + g0[1]) + (g0[2] + g0[3]);
+              lane1 += (g1[0] + g1[1]) + (g1[2] + g1[3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                lane0 += g0[j] & vmask[j];
+                lane1 += g1[j] & vmask[j];
+              }
+            }
+            cnt_n += nv;
+            if (++since_fold == 63) {
+              cnt_ge0 += byte_sum(lane0);
+              cnt_ge1 += byte_sum(lane1);
+              lane0 = lane1 = 0;
+              since_fold = 0;
+            }
           } else if (a.reduce == RED_SUM) {
             uint32_t s4 = 0;
 #pragma unroll
@@ -183,15 +256,19 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
           }
           if (a.out) {
             uint8_t *orow = a.out + y * a.out_pitch + xo;
-            if (nv == 16) {
+            if (full) {
               __stcs(reinterpret_cast<uint4 *>(orow), make_uint4(w[0], w[1], w[2], w[3]));
             } else {
-              for (int k = 0; k < nv; ++k) orow[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+#pragma unroll
+              for (int k = 0; k < 16; ++k)
+                if (k < nv) orow[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
             }
           }
         }
       }
     }
+    cnt_ge0 += byte_sum(lane0);
+    cnt_ge1 += byte_sum(lane1);
   }
 
   if (a.reduce == RED_NONE) return;
@@ -199,12 +276,12 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long r0v, r1v, r2v;
   if (a.reduce == RED_COUNT3) {
-    const uint32_t s1 = __reduce_add_sync(0xFFFFFFFFu, c1);
-    const uint32_t s2 = __reduce_add_sync(0xFFFFFFFFu, c2);
-    const uint32_t sn = __reduce_add_sync(0xFFFFFFFFu, cn);
-    r0v = (unsigned long long)(sn - s1 - s2);
-    r1v = s1;
-    r2v = s2;
+    const uint32_t s0 = __reduce_add_sync(0xFFFFFFFFu, cnt_ge0);
+    const uint32_t s1 = __reduce_add_sync(0xFFFFFFFFu, cnt_ge1);
+    const uint32_t sn = __reduce_add_sync(0xFFFFFFFFu, cnt_n);
+    r0v = (unsigned long long)(sn - s0);  // label 0
+    r1v = (unsigned long long)(s0 - s1);  // label 1
+    r2v = s1;                             // label 2
   } else {
     unsigned long long s = vsum;
 #pragma unroll
@@ -218,46 +295,101 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
     red_smem[warp][2] = r2v;
   }
   __syncthreads();
+  __shared__ bool is_last;
+  const int nout = a.reduce == RED_COUNT3 ? 3 : 1;
   if (threadIdx.x == 0) {
-    unsigned long long t0 = 0, t1 = 0, t2 = 0;
+    unsigned long long t[3] = {0, 0, 0};
     const int nw = (blockDim.x + 31) >> 5;
     for (int i = 0; i < nw; ++i) {
-      t0 += red_smem[i][0];
-      t1 += red_smem[i][1];
-      t2 += red_smem[i][2];
+      t[0] += red_smem[i][0];
+      t[1] += red_smem[i][1];
+      t[2] += red_smem[i][2];
     }
-    if (a.reduce == RED_COUNT3) {
-      if (t0) atomicAdd(a.red + 0, t0);
-      if (t1) atomicAdd(a.red + 1, t1);
-      if (t2) atomicAdd(a.red + 2, t2);
-    } else if (t0) {
-      atomicAdd(a.red, t0);
+    if (a.partials == nullptr) {
+      for (int k = 0; k < nout; ++k)
+        if (t[k]) atomicAdd(a.red + k, t[k]);
+      is_last = false;
+    } else {
+      for (int k = 0; k < 3; ++k) a.partials[3 * blockIdx.x + k] = t[k];
+      __threadfence();
+      is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
+  }
+  __syncthreads();
+  if (!is_last) return;
+  // last CTA: sum every CTA's partial result (integer sums: any order gives the same value)
+  __threadfence();
+  unsigned long long t[3] = {0, 0, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int k = 0; k < 3; ++k) t[k] += __ldcg(a.partials + 3 * b + k);
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xFFFFFFFFu, t[k], o);
+  }
+  __syncthreads();  // red_smem is reused
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) red_smem[warp][k] = t[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nout; ++k) {
+      unsigned long long v = 0;
+      for (int i = 0; i < nw; ++i) v += red_smem[i][k];
+      a.red[k] = v;
+    }
+    *a.ticket = 0u;  // ready for the next launch on this workspace
   }
 }
 
+template <int NN, bool MIR, int U>
+const void *kernel_ptr() {
+  return (const void *)chain_kernel<NN, MIR, U>;
+}
+
 template <int NN, bool MIR>
-cudaError_t launch_u(const ChainArgs &a, int unroll, int grid, int block, cudaStream_t s) {
+const void *pick_u(int unroll) {
   switch (unroll) {
-    case 1: chain_kernel<NN, MIR, 1><<<grid, block, 0, s>>>(a); break;
-    case 2: chain_kernel<NN, MIR, 2><<<grid, block, 0, s>>>(a); break;
-    case 8: chain_kernel<NN, MIR, 8><<<grid, block, 0, s>>>(a); break;
-    default: chain_kernel<NN, MIR, 4><<<grid, block, 0, s>>>(a); break;
+    case 1: return kernel_ptr<NN, MIR, 1>();
+    case 2: return kernel_ptr<NN, MIR, 2>();
+    case 8: return kernel_ptr<NN, MIR, 8>();
+    default: return kernel_ptr<NN, MIR, 4>();
   }
-  return cudaGetLastError();
+}
+
+const void *pick(int n_noise, bool mir, int unroll) {
+  switch (n_noise) {
+    case 0: return mir ? pick_u<0, true>(unroll) : pick_u<0, false>(unroll);
+    case 1: return mir ? pick_u<1, true>(unroll) : pick_u<1, false>(unroll);
+    case 2: return mir ? pick_u<2, true>(unroll) : pick_u<2, false>(unroll);
+    default: return nullptr;
+  }
 }
 
 }  // namespace
 
+int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block) {
+  static int cache[3][2][4][9] = {};  // [noise][mirror][unroll 1,2,4,8][block / 32, up to 256]
+  const int ui = unroll == 1 ? 0 : unroll == 2 ? 1 : unroll == 8 ? 3 : 2;
+  const int bi = block / 32;
+  if (n_noise < 0 || n_noise > 2 || bi < 1 || bi > 8) return 1;
+  int &c = cache[n_noise][mirror ? 1 : 0][ui][bi];
+  if (c) return c;
+  const void *fn = pick(n_noise, mirror, unroll);
+  int nb = 0;
+  if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  c = nb > 0 ? nb : 1;
+  return c;
+}
+
 cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  const bool mir = a.mirror != 0;
-  switch (n_noise) {
-    case 0: return mir ? launch_u<0, true>(a, unroll, grid, block, s) : launch_u<0, false>(a, unroll, grid, block, s);
-    case 1: return mir ? launch_u<1, true>(a, unroll, grid, block, s) : launch_u<1, false>(a, unroll, grid, block, s);
-    case 2: return mir ? launch_u<2, true>(a, unroll, grid, block, s) : launch_u<2, false>(a, unroll, grid, block, s);
-    default: return cudaErrorInvalidValue;
-  }
+  const void *fn = pick(n_noise, a.mirror != 0, unroll);
+  if (!fn) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace mrw

@@ -4,9 +4,13 @@
 //
 // Partitioning: the bodies are split into one contiguous range per CTA (the paper's partitions,
 // here one per SM-resident CTA); each thread owns `B` bodies of its CTA's range, strided by the
-// block size so that loads and stores stay coalesced. Every CTA streams all positions through a
-// shared-memory tile (the COPY vector) and sums j in index order, so each body's sum has the same
-// order whatever the launch shape — Loop(k) and k single steps give bit-identical states.
+// group size so that loads and stores stay coalesced. A CTA has four warp groups; each streams a
+// fixed quarter of all positions (the COPY vector) through its own shared-memory tile, so an SM
+// runs four times as many warps as 65536 bodies alone would give it. Arithmetic uses the packed
+// f32x2 instructions of sm_100+: the two lanes of a register pair hold an even j and the next odd
+// j, halving the instruction count per interaction. Each body's sum has a fixed order that depends
+// on N only (pairs in index order per lane, lanes added, quarters added in order), so Loop(k) and k
+// single steps, and every launch shape, give bit-identical states.
 //
 // Loop (Section 2.1; the paper evaluates the condition on the host, Section 3.1): here the
 // condition is evaluated on the device. One step is two kernels (drift, then force + kick):
@@ -18,61 +22,140 @@
 namespace mrw {
 namespace {
 
-constexpr int kTile = 256;
+constexpr int kJSplit = 4;   // warp groups per CTA, each summing a fixed quarter of the j range
+constexpr int kTileJ = 256;  // j bodies per shared-memory tile and group
 
+// Packed FP32 pairs (sm_100+ f32x2 instructions): lane 0 holds an even j, lane 1 the next odd j.
+__device__ __forceinline__ unsigned long long pk(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void group_sync(int g, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(nthreads) : "memory");
+}
+
+// First j of group g (even, so pairs never straddle two groups); group kJSplit ends at n.
+__device__ __forceinline__ int group_start(int n, int g) {
+  return g >= kJSplit ? n : (int)(((int64_t)n * g / kJSplit) & ~1LL);
+}
+
+// Accelerations of the CTA's bodies [lo, hi) with hi - lo <= T * B, T = blockDim.x / kJSplit.
+// Every body's sum: per group, pairs (j, j+1) accumulated lane-wise in index order, lanes added;
+// then the groups' partial sums added in group order. The order depends on n only.
 template <int B>
-__global__ void __launch_bounds__(256) force_kernel(const float4 *__restrict__ x, float4 *__restrict__ v,
-                                                    float4 *__restrict__ a, int n, float G, float eps2, float hdt,
-                                                    int kick) {
-  __shared__ float4 tile[kTile];
+__global__ void __launch_bounds__(B == 4 ? 512 : 1024, 1) force_kernel(const float4 *__restrict__ x, float4 *__restrict__ v,
+                                                        float4 *__restrict__ a, int n, float G, float eps2,
+                                                        float hdt, int kick) {
+  __shared__ __align__(16) float tile[kJSplit][4][kTileJ];
+  extern __shared__ float part[];  // [kJSplit][3][T * B]
+  const int T = blockDim.x / kJSplit;
+  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   const int64_t lo = (int64_t)n * blockIdx.x / gridDim.x;
   const int64_t hi = (int64_t)n * (blockIdx.x + 1) / gridDim.x;
-  float3 xi[B];
-  float3 acc[B];
-  int idx[B];
+
+  unsigned long long xi[B], yi[B], zi[B], ax[B], ay[B], az[B];
 #pragma unroll
   for (int b = 0; b < B; ++b) {
-    const int64_t i = lo + threadIdx.x + (int64_t)b * blockDim.x;
-    idx[b] = i < hi ? (int)i : -1;
-    const float4 p = idx[b] >= 0 ? x[idx[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    xi[b] = make_float3(p.x, p.y, p.z);
-    acc[b] = make_float3(0.f, 0.f, 0.f);
+    const int64_t i = lo + t + (int64_t)b * T;
+    const float4 p = i < hi ? x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[b] = pk(p.x, p.x);
+    yi[b] = pk(p.y, p.y);
+    zi[b] = pk(p.z, p.z);
+    ax[b] = ay[b] = az[b] = 0ull;
   }
-  for (int j0 = 0; j0 < n; j0 += kTile) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+  const unsigned long long e2 = pk(eps2, eps2);
+  const int j_begin = group_start(n, g), j_end = group_start(n, g + 1);
+  float *tx = tile[g][0], *ty = tile[g][1], *tz = tile[g][2], *tm = tile[g][3];
+  for (int j0 = j_begin; j0 < j_end; j0 += kTileJ) {
+    group_sync(g, T);
+    for (int k = t; k < kTileJ; k += T) {
       // zero-mass padding adds exactly zero to every sum
-      tile[k] = j0 + k < n ? x[j0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 q = j0 + k < j_end ? x[j0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      tx[k] = q.x;
+      ty[k] = q.y;
+      tz[k] = q.z;
+      tm[k] = q.w;
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < kTile; ++k) {
-      const float4 pj = tile[k];
+    group_sync(g, T);
+    const int kend = min(kTileJ, j_end - j0 + 1) & ~1;  // pairs covering the valid j of this tile
+#pragma unroll 4
+    for (int k = 0; k < kend; k += 2) {
+      const unsigned long long x2 = *reinterpret_cast<const unsigned long long *>(tx + k);
+      const unsigned long long y2 = *reinterpret_cast<const unsigned long long *>(ty + k);
+      const unsigned long long z2 = *reinterpret_cast<const unsigned long long *>(tz + k);
+      const unsigned long long m2 = *reinterpret_cast<const unsigned long long *>(tm + k);
 #pragma unroll
       for (int b = 0; b < B; ++b) {
-        const float dx = pj.x - xi[b].x;
-        const float dy = pj.y - xi[b].y;
-        const float dz = pj.z - xi[b].z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        const float inv = rsqrtf(r2);
-        const float s = (pj.w * inv) * (inv * inv);
-        acc[b].x = fmaf(s, dx, acc[b].x);
-        acc[b].y = fmaf(s, dy, acc[b].y);
-        acc[b].z = fmaf(s, dz, acc[b].z);
+        const unsigned long long dx = sub2(x2, xi[b]);
+        const unsigned long long dy = sub2(y2, yi[b]);
+        const unsigned long long dz = sub2(z2, zi[b]);
+        const unsigned long long r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+        const float2 rr = upk(r2);
+        const unsigned long long inv = pk(rsqrt_approx(rr.x), rsqrt_approx(rr.y));
+        const unsigned long long s = mul2(mul2(m2, inv), mul2(inv, inv));
+        ax[b] = fma2(s, dx, ax[b]);
+        ay[b] = fma2(s, dy, ay[b]);
+        az[b] = fma2(s, dz, az[b]);
       }
     }
   }
+  const int nb = T * B;
 #pragma unroll
   for (int b = 0; b < B; ++b) {
-    if (idx[b] < 0) continue;
-    const float4 ai = make_float4(G * acc[b].x, G * acc[b].y, G * acc[b].z, 0.f);
-    a[idx[b]] = ai;
+    const float2 px = upk(ax[b]), py = upk(ay[b]), pz = upk(az[b]);
+    const int li = t + b * T;
+    part[(g * 3 + 0) * nb + li] = px.x + px.y;
+    part[(g * 3 + 1) * nb + li] = py.x + py.y;
+    part[(g * 3 + 2) * nb + li] = pz.x + pz.y;
+  }
+  __syncthreads();
+  if (g != 0) return;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int li = t + b * T;
+    const int64_t i = lo + li;
+    if (i >= hi) continue;
+    float sx = part[0 * nb + li], sy = part[1 * nb + li], sz = part[2 * nb + li];
+#pragma unroll
+    for (int q = 1; q < kJSplit; ++q) {
+      sx += part[(q * 3 + 0) * nb + li];
+      sy += part[(q * 3 + 1) * nb + li];
+      sz += part[(q * 3 + 2) * nb + li];
+    }
+    const float4 ai = make_float4(G * sx, G * sy, G * sz, 0.f);
+    a[i] = ai;
     if (kick) {
-      float4 vi = v[idx[b]];
+      float4 vi = v[i];
       vi.x = fmaf(hdt, ai.x, vi.x);
       vi.y = fmaf(hdt, ai.y, vi.y);
       vi.z = fmaf(hdt, ai.z, vi.z);
-      v[idx[b]] = vi;
+      v[i] = vi;
     }
   }
 }
@@ -130,12 +213,29 @@ void *force_fn(int b) {
 
 }  // namespace
 
+size_t force_smem(int bpt, int block) { return (size_t)kJSplit * 3 * (block / kJSplit) * bpt * sizeof(float); }
+
+cudaError_t force_prepare(int bpt) {
+  static bool done[5] = {};
+  if (bpt < 1 || bpt > 4) return cudaErrorInvalidValue;
+  if (!done[bpt]) {
+    cudaError_t e = cudaFuncSetAttribute(force_fn(bpt), cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    done[bpt] = true;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_nbody_force(const NBodyParams &p, int kick, int bpt, int grid, int block, cudaStream_t s) {
+  if (block % (32 * kJSplit) || block > (bpt == 4 ? 512 : 1024)) return cudaErrorInvalidValue;
+  cudaError_t e = force_prepare(bpt);
+  if (e != cudaSuccess) return e;
   const float hdt = 0.5f * p.dt;
+  const size_t sm = force_smem(bpt, block);
   switch (bpt) {
-    case 1: force_kernel<1><<<grid, block, 0, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
-    case 4: force_kernel<4><<<grid, block, 0, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
-    default: force_kernel<2><<<grid, block, 0, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
+    case 1: force_kernel<1><<<grid, block, sm, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
+    case 4: force_kernel<4><<<grid, block, sm, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
+    default: force_kernel<2><<<grid, block, sm, s>>>(p.x, p.v, p.a, p.n, p.G, p.eps2, hdt, kick); break;
   }
   return cudaGetLastError();
 }
@@ -219,7 +319,9 @@ cudaError_t build_nbody_loop_graph(const NBodyParams &p, LoopCtrl *ctrl, int64_t
     kp.func = force_fn(bpt);
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(block);
+    kp.sharedMemBytes = (unsigned)force_smem(bpt, block);
     kp.kernelParams = args;
+    MRW_TRY(force_prepare(bpt));
     MRW_TRY(cudaGraphAddKernelNode(&force_node, body, &drift_node, 1, &kp));
   }
   cudaError_t e = cudaGraphInstantiate(exec, graph, 0);

@@ -119,48 +119,130 @@ __device__ __forceinline__ Tile locate(const StencilArgs &a, int64_t t) {
   return g;
 }
 
+// ---- per-pixel ops (general paths: edge quads, suffixes, more than two noise stages) ----
 __device__ __forceinline__ uint32_t apply_ops_px(const ChainOp *ops, int n, uint32_t p, int col, int W, uint32_t y,
-                                                 const uint32_t *colhash, uint32_t seed_xor) {
-  int kn = 0;
+                                                 uint32_t seed_xor) {
   for (int i = 0; i < n; ++i) {
-    const ChainOp op = ops[i];
-    if (op.kind == OP_SOLARISE) {
+    const int kind = ops[i].kind;
+    if (kind == OP_SOLARISE) {
       p = p < 128u ? p : 255u - p;
-    } else if (op.kind == OP_THRESH) {
-      p = (p >= (op.t & 0xFFu) ? 1u : 0u) + (p >= ((op.t >> 8) & 0xFFu) ? 1u : 0u);
-    } else if (op.kind == OP_NOISE) {
-      uint32_t c;
-      if (colhash != nullptr && kn < kMaxNoisePerGroup) {
-        c = colhash[kn];
-      } else {
-        const uint32_t x = op.flip ? (uint32_t)(W - 1 - col) : (uint32_t)col;
-        c = fmix32(fmix32(op.seed ^ seed_xor) ^ x);
-      }
-      const uint32_t hh = fmix32(c ^ y);
-      const int q = (int)p + (int)(hh % 41u) - 20;
+    } else if (kind == OP_THRESH) {
+      const uint32_t t = ops[i].t;
+      p = (p >= (t & 0xFFu) ? 1u : 0u) + (p >= ((t >> 8) & 0xFFu) ? 1u : 0u);
+    } else if (kind == OP_NOISE) {
+      const uint32_t x = ops[i].flip ? (uint32_t)(W - 1 - col) : (uint32_t)col;
+      const uint32_t h = fmix32(fmix32(fmix32(ops[i].seed ^ seed_xor) ^ x) ^ y);
+      const int q = (int)p + (int)(h % 41u) - 20;
       p = (uint32_t)min(max(q, 0), 255);
-      ++kn;
     }
   }
   return p;
 }
 
+// ---- word (4-pixel) ops ----
+constexpr uint32_t kHi = 0x80808080u;
+
+__device__ __forceinline__ uint32_t solarise4(uint32_t w) { return w ^ (((w >> 7) & 0x01010101u) * 0xFFu); }
+
+// 0x80 per byte where a >= t (borrow-free byte compare; tlo = t & 0x7F7F7F7F)
+__device__ __forceinline__ uint32_t ge4(uint32_t a, uint32_t t, uint32_t tlo) {
+  const uint32_t d = (a | kHi) - tlo;
+  return ((a & ~t) | (~(a ^ t) & d)) & kHi;
+}
+
+__device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t noise_byte(uint32_t p, uint32_t colpre, uint32_t ypre) {
+  const uint32_t h = fmix32_tail(colpre ^ ypre);
+  const int q = (int)p + (int)(h % 41u) - 20;
+  return (uint32_t)min(max(q, 0), 255);
+}
+
+// Ops on the 4 pixels of a word whose columns are c0..c0+3 (clamped columns gc[k] for the hash);
+// colpre[kn] holds the 4 column hashes of noise op kn (already split as c ^ (c >> 16)).
+struct Cols4 {
+  int c[4];
+};
+
+__device__ __forceinline__ uint32_t apply_ops_word(const ChainOp *ops, int n, uint32_t w, uint4 colpre0,
+                                                   uint4 colpre1, uint32_t ypre, Cols4 gc, int W,
+                                                   uint32_t seed_xor) {
+  int kn = 0;
+  for (int i = 0; i < n; ++i) {
+    const int kind = ops[i].kind;
+    if (kind == OP_SOLARISE) {
+      w = solarise4(w);
+    } else if (kind == OP_THRESH) {
+      const uint32_t t = ops[i].t;
+      const uint32_t t0 = (t & 0xFFu) * 0x01010101u, t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
+      w = (ge4(w, t0, t0 & 0x7F7F7F7Fu) >> 7) + (ge4(w, t1, t1 & 0x7F7F7F7Fu) >> 7);
+    } else if (kind == OP_NOISE) {
+      uint32_t c[4];
+      if (kn < kMaxNoisePerGroup) {
+        const uint4 v = kn == 0 ? colpre0 : colpre1;
+        c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t x = ops[i].flip ? (uint32_t)(W - 1 - gc.c[k]) : (uint32_t)gc.c[k];
+          const uint32_t cc = fmix32(fmix32(ops[i].seed ^ seed_xor) ^ x);
+          c[k] = cc ^ (cc >> 16);
+        }
+      }
+      w = noise_byte(w & 0xFFu, c[0], ypre) | (noise_byte((w >> 8) & 0xFFu, c[1], ypre) << 8) |
+          (noise_byte((w >> 16) & 0xFFu, c[2], ypre) << 16) | (noise_byte(w >> 24, c[3], ypre) << 24);
+      ++kn;
+    }
+  }
+  return w;
+}
+
+// 4 bytes of a shared-memory row starting at byte offset o (o >= 0, any alignment; the row is
+// 4-byte aligned and holds at least o + 4 bytes).
+__device__ __forceinline__ uint32_t load4(const uint8_t *row, int o) {
+  const uint32_t *r32 = reinterpret_cast<const uint32_t *>(row);
+  const uint32_t lo = r32[o >> 2];
+  if ((o & 3) == 0) return lo;
+  const uint32_t hi = r32[(o >> 2) + 1];
+  return __funnelshift_r(lo, hi, 8 * (o & 3));
+}
+
+// Store the first nb (1..4) bytes of w at p (p 4-byte aligned when nb == 4).
+__device__ __forceinline__ void store4(uint8_t *p, uint32_t w, int nb) {
+  if (nb >= 4) {
+    *reinterpret_cast<uint32_t *>(p) = w;
+  } else {
+    for (int k = 0; k < nb; ++k) p[k] = (uint8_t)(w >> (8 * k));
+  }
+}
+
+template <int TW, int H>
 __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__ StencilArgs a) {
+  constexpr int QP = (TW + 2 * H + 15) & ~15;  // Q row pitch (bytes) and column-hash row length
+  constexpr int QW4 = (TW + 2 * H + 3) / 4;    // quads per Q row
+  constexpr int RQ = TW / 4;                   // quads per output row
+  constexpr int RPT = 4;                       // output rows per blur task
   extern __shared__ __align__(128) uint8_t smem[];
-  const int BW = a.box_w, BH = a.box_h, TH = a.tile_h, TW = a.tile_w, h = a.halo;
-  const int QP = (TW + 2 * h + 15) & ~15;  // Q row pitch
-  const int nsq = TW + 2 * h;              // Q columns per tile (max)
-  uint8_t *box[2] = {smem, smem + BH * BW};
+  const int BW = a.box_w, BH = a.box_h, TH = a.tile_h;
+  // two TMA destination buffers: buffer b starts at smem + b * BH * BW
   uint8_t *qt = smem + 2 * BH * BW;
   uint8_t *rt = qt + BH * QP;
-  uint32_t *qcol = reinterpret_cast<uint32_t *>(rt + TH * TW);  // [kMaxNoisePerGroup][nsq]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(qcol + kMaxNoisePerGroup * ((nsq + 1) & ~1));
+  uint32_t *qcol = reinterpret_cast<uint32_t *>(rt + TH * TW);  // [kMaxNoisePerGroup][QP]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(qcol + kMaxNoisePerGroup * QP);
   __shared__ int64_t s_tile[2];
   __shared__ int s_fail;
 
   const int tid = threadIdx.x;
   const uint32_t box_bytes = (uint32_t)(BW * BH);
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phases = 0u;  // bit b = parity of buffer b's next completion
+  // no suffix: the last phase writes the output straight from registers
+  const bool direct = a.nsuf == 0 && a.msuf == 0;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -172,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
     if (t < a.total_tiles) {
       const Tile g = locate(a, t);
       mbar_expect_tx(&bar[0], box_bytes);
-      tma_load_3d(box[0], a.maps + g.inst, g.bx, g.by, g.z, &bar[0]);
+      tma_load_3d(smem, a.maps + g.inst, g.bx, g.by, g.z, &bar[0]);
     }
   }
   __syncthreads();
@@ -192,125 +274,140 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
         const Tile gn = locate(a, tn);
         fence_proxy_async();
         mbar_expect_tx(&bar[cur ^ 1], box_bytes);
-        tma_load_3d(box[cur ^ 1], a.maps + gn.inst, gn.bx, gn.by, gn.z, &bar[cur ^ 1]);
+        tma_load_3d(smem + (cur ^ 1) * BH * BW, a.maps + gn.inst, gn.bx, gn.by, gn.z, &bar[cur ^ 1]);
       }
-      if (!mbar_wait_bounded(&bar[cur], phase[cur], a.wait_polls ? a.wait_polls - 1 : kWaitPolls)) s_fail = 1;
+      if (!mbar_wait_bounded(&bar[cur], (phases >> cur) & 1u, a.wait_polls ? a.wait_polls - 1 : kWaitPolls))
+        s_fail = 1;
     }
-    // Column hashes of the prefix's noise ops for this tile's Q columns.
-    const int qcols = g.cols + 2 * h;
+    // Column hashes of the prefix's noise ops for this tile's Q columns: c ^ (c >> 16) with
+    // c = F(F(seed ^ instance seed) ^ x), x the op's column coordinate of the clamped Q column.
+    const int qcols = g.cols + 2 * H;
     {
       int kn = 0;
       for (int i = 0; i < a.npre && kn < kMaxNoisePerGroup; ++i) {
         if (a.pre[i].kind != OP_NOISE) continue;
         const uint32_t fs = fmix32(a.pre[i].seed ^ inst.seed_xor);
-        for (int j = tid; j < qcols; j += kBlock) {
-          const int gc = min(max(g.r0 - h + j, 0), g.W - 1);
-          const uint32_t x = a.pre[i].flip ? (uint32_t)(g.W - 1 - gc) : (uint32_t)gc;
-          qcol[kn * nsq + j] = fmix32(fs ^ x);
+        const int flip = a.pre[i].flip;
+        for (int j = tid; j < 4 * QW4; j += kBlock) {
+          const int gc = min(max(g.r0 - H + j, 0), g.W - 1);
+          const uint32_t x = flip ? (uint32_t)(g.W - 1 - gc) : (uint32_t)gc;
+          const uint32_t c = fmix32(fs ^ x);
+          qcol[kn * QP + j] = c ^ (c >> 16);
         }
         ++kn;
       }
     }
     __syncthreads();
     if (s_fail) break;
-    phase[cur] ^= 1u;
+    phases ^= 1u << cur;
 
-    // Q tile: prefix applied to the clamped (replicated-edge) neighbourhood of the output tile.
-    const uint8_t *bx = box[cur];
-    const int qrows = g.rows + 2 * h;
+    const uint8_t *bx = smem + cur * BH * BW;
     const uint32_t plane_row0 = (uint32_t)g.z * (uint32_t)g.H;
-    for (int e = tid; e < qrows * qcols; e += kBlock) {
-      const int i = e / qcols, j = e - i * qcols;
-      const int gy = min(max(g.y0 - h + i, 0), g.H - 1);
-      const int gc = min(max(g.r0 - h + j, 0), g.W - 1);
-      const int ic = a.mpre ? g.W - 1 - gc : gc;
-      uint32_t p = bx[(gy - g.by) * BW + (ic - g.bx)];
-      uint32_t chv[kMaxNoisePerGroup];
-#pragma unroll
-      for (int k = 0; k < kMaxNoisePerGroup; ++k) chv[k] = qcol[k * nsq + j];
-      p = apply_ops_px(a.pre, a.npre, p, gc, g.W, plane_row0 + (uint32_t)gy, chv, inst.seed_xor);
-      qt[i * QP + j] = (uint8_t)p;
-    }
-    __syncthreads();
-
-    const uint8_t *rsrc;  // R tile (blur output, or Q itself without a blur), pitch rpitch
-    int rpitch;
-    if (h == 2) {
-      // 5x5 box sums: each thread owns 4 adjacent R columns and a run of rows; horizontal 5-sums
-      // per Q row from two aligned words, vertical sums over a sliding window of five rows.
-      const int quads = (g.cols + 3) >> 2;
-      const int rows_per = 4;
-      const int row_groups = (g.rows + rows_per - 1) / rows_per;
-      for (int e = tid; e < quads * row_groups; e += kBlock) {
-        const int jq = e % quads, rg = e / quads;
-        const int i0 = rg * rows_per;
-        const int ni = min(rows_per, g.rows - i0);
-        uint32_t hs[rows_per + 4][4];
-#pragma unroll
-        for (int d = 0; d < rows_per + 4; ++d) {
-          if (d < ni + 4) {
-            const uint32_t *qw = reinterpret_cast<const uint32_t *>(qt + (i0 + d) * QP + 4 * jq);
-            const uint32_t lo = qw[0], hi = qw[1];
-            const uint32_t b0 = lo & 0xFF, b1 = (lo >> 8) & 0xFF, b2 = (lo >> 16) & 0xFF, b3 = lo >> 24;
-            const uint32_t b4 = hi & 0xFF, b5 = (hi >> 8) & 0xFF, b6 = (hi >> 16) & 0xFF, b7 = hi >> 24;
-            hs[d][0] = b0 + b1 + b2 + b3 + b4;
-            hs[d][1] = hs[d][0] - b0 + b5;
-            hs[d][2] = hs[d][1] - b1 + b6;
-            hs[d][3] = hs[d][2] - b2 + b7;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < rows_per; ++i) {
-          if (i < ni) {
-            uint32_t outw = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const uint32_t s = hs[i][c] + hs[i + 1][c] + hs[i + 2][c] + hs[i + 3][c] + hs[i + 4][c];
-              outw |= ((s + 12u) / 25u) << (8 * c);
-            }
-            *reinterpret_cast<uint32_t *>(rt + (i0 + i) * TW + 4 * jq) = outw;
-          }
-        }
-      }
-      __syncthreads();
-      rsrc = rt;
-      rpitch = TW;
-    } else {
-      rsrc = qt;
-      rpitch = QP;
-    }
-
-    // Suffix and store: one 16-byte output segment per thread and row.
-    const int segs = (g.cols + 15) >> 4;
     uint8_t *obase = a.out_base + inst.out_off + ((int64_t)g.z * g.H + g.y0) * inst.pitch_out + g.x0;
-    for (int e = tid; e < segs * g.rows; e += kBlock) {
-      const int i = e / segs, c = e - i * segs;
-      const int nv = min(16, g.cols - 16 * c);
-      uint8_t vb[16];
-      const uint8_t *rrow = rsrc + i * rpitch;
+
+    // Phase A: Q words (prefix applied to the clamped neighbourhood), 4 columns per task.
+    const int qrows = g.rows + 2 * H;
+    const int nq4 = (qcols + 3) >> 2;
+    for (int e = tid; e < qrows * QW4; e += kBlock) {
+      const int i = e / QW4, jq = e - i * QW4;
+      if (jq >= nq4) continue;
+      const int gy = min(max(g.y0 - H + i, 0), g.H - 1);
+      const uint8_t *brow = bx + (gy - g.by) * BW;
+      const int c0 = g.r0 - H + 4 * jq;
+      Cols4 gc;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        // output column x0+16c+k reads R local column (msuf: mirrored within the tile's span)
-        const int lc = a.msuf ? g.cols - 1 - 16 * c - k : 16 * c + k;
-        vb[k] = k < nv ? rrow[lc] : 0;
-      }
-      if (a.nsuf > 0) {
-        const uint32_t y = plane_row0 + (uint32_t)(g.y0 + i);
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (k < nv) vb[k] = (uint8_t)apply_ops_px(a.suf, a.nsuf, vb[k], g.x0 + 16 * c + k, g.W, y, nullptr,
-                                                    inst.seed_xor);
-      }
-      uint8_t *orow = obase + (int64_t)i * inst.pitch_out + 16 * c;
-      if (nv == 16) {
-        uint4 o;
-        o.x = vb[0] | (vb[1] << 8) | (vb[2] << 16) | ((uint32_t)vb[3] << 24);
-        o.y = vb[4] | (vb[5] << 8) | (vb[6] << 16) | ((uint32_t)vb[7] << 24);
-        o.z = vb[8] | (vb[9] << 8) | (vb[10] << 16) | ((uint32_t)vb[11] << 24);
-        o.w = vb[12] | (vb[13] << 8) | (vb[14] << 16) | ((uint32_t)vb[15] << 24);
-        __stcs(reinterpret_cast<uint4 *>(orow), o);
+      for (int k = 0; k < 4; ++k) gc.c[k] = min(max(c0 + k, 0), g.W - 1);
+      uint32_t w;
+      if (c0 >= 0 && c0 + 3 <= g.W - 1 && 4 * jq + 4 <= qcols) {
+        // a whole quad inside the image and inside the tile's Q range: one (funnel-shifted) word
+        if (!a.mpre) {
+          w = load4(brow, c0 - g.bx);
+        } else {
+          w = __byte_perm(load4(brow, g.W - 4 - c0 - g.bx), 0, 0x0123);
+        }
       } else {
-        for (int k = 0; k < nv; ++k) orow[k] = vb[k];
+        // image edges (replicated columns) and the tile's ragged last quad
+        w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (4 * jq + k < qcols) {
+            const int ic = a.mpre ? g.W - 1 - gc.c[k] : gc.c[k];
+            w |= (uint32_t)brow[ic - g.bx] << (8 * k);
+          }
+        }
+      }
+      const uint32_t y = plane_row0 + (uint32_t)gy;
+      const uint4 cp0 = *reinterpret_cast<const uint4 *>(qcol + 4 * jq);
+      const uint4 cp1 = *reinterpret_cast<const uint4 *>(qcol + QP + 4 * jq);
+      w = apply_ops_word(a.pre, a.npre, w, cp0, cp1, y ^ (y >> 16), gc, g.W, inst.seed_xor);
+      if (H == 0 && direct) {
+        store4(obase + (int64_t)i * inst.pitch_out + 4 * jq, w, min(4, g.cols - 4 * jq));
+      } else {
+        *reinterpret_cast<uint32_t *>(qt + i * QP + 4 * jq) = w;
+      }
+    }
+    if (!(H == 0 && direct)) {
+      __syncthreads();
+      const uint8_t *rsrc = qt;  // R tile: the blur output, or Q itself without a blur
+      int rpitch = QP;
+      if (H == 2) {
+        // Phase B: 5x5 box sums. A task is 4 output columns x RPT rows: horizontal 5-sums of each
+        // Q row in packed 16-bit lanes (h0,h2) and (h1,h3), vertical sums over a sliding window.
+        const int nr4 = (g.cols + 3) >> 2;
+        const int ntask = ((g.rows + RPT - 1) / RPT) * RQ;
+        for (int e = tid; e < ntask; e += kBlock) {
+          const int rg = e / RQ, jr = e - rg * RQ;
+          if (jr >= nr4) continue;
+          const int i0 = rg * RPT, ni = min(RPT, g.rows - i0);
+          uint32_t h02[RPT + 4], h13[RPT + 4];
+          uint32_t s02 = 0, s13 = 0;
+#pragma unroll
+          for (int d = 0; d < RPT + 4; ++d) {
+            if (d < ni + 4) {
+              const uint32_t *qw = reinterpret_cast<const uint32_t *>(qt + (i0 + d) * QP + 4 * jr);
+              const uint32_t lo = qw[0], hi = qw[1];
+              const uint32_t E = lo & 0x00FF00FFu, O = (lo >> 8) & 0x00FF00FFu;
+              const uint32_t E2 = hi & 0x00FF00FFu, O2 = (hi >> 8) & 0x00FF00FFu;
+              const uint32_t A = E + O, A2 = E2 + O2, P = __byte_perm(A, A2, 0x5432);
+              h02[d] = A + P + E2;
+              h13[d] = O + P + A2;
+              s02 += h02[d];
+              s13 += h13[d];
+              if (d >= 5) {
+                s02 -= h02[d - 5];
+                s13 -= h13[d - 5];
+              }
+              if (d >= 4) {
+                const int r = i0 + d - 4;
+                const uint32_t o = ((s02 & 0xFFFFu) + 12u) / 25u | ((((s13 & 0xFFFFu) + 12u) / 25u) << 8) |
+                                   ((((s02 >> 16) + 12u) / 25u) << 16) | ((((s13 >> 16) + 12u) / 25u) << 24);
+                if (direct) {
+                  store4(obase + (int64_t)r * inst.pitch_out + 4 * jr, o, min(4, g.cols - 4 * jr));
+                } else {
+                  *reinterpret_cast<uint32_t *>(rt + r * TW + 4 * jr) = o;
+                }
+              }
+            }
+          }
+        }
+        rsrc = rt;
+        rpitch = TW;
+        if (!direct) __syncthreads();
+      }
+      if (!direct) {
+        // Suffix and store (general path): one 16-byte output segment per thread and row.
+        const int segs = (g.cols + 15) >> 4;
+        for (int e = tid; e < segs * g.rows; e += kBlock) {
+          const int i = e / segs, c = e - i * segs;
+          const int nv = min(16, g.cols - 16 * c);
+          const uint8_t *rrow = rsrc + i * rpitch;
+          const uint32_t y = plane_row0 + (uint32_t)(g.y0 + i);
+          uint8_t *orow = obase + (int64_t)i * inst.pitch_out + 16 * c;
+          for (int k = 0; k < nv; ++k) {
+            const int lc = a.msuf ? g.cols - 1 - 16 * c - k : 16 * c + k;
+            orow[k] = (uint8_t)apply_ops_px(a.suf, a.nsuf, rrow[lc], g.x0 + 16 * c + k, g.W, y, inst.seed_xor);
+          }
+        }
       }
     }
     __syncthreads();
@@ -320,8 +417,23 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
   if (s_fail && tid == 0) {
     atomicOr(a.status, 1u);
     // let the copies this CTA issued land before it leaves (bounded as well)
-    if (s_tile[cur ^ 1] < a.total_tiles) (void)mbar_wait_bounded(&bar[cur ^ 1], phase[cur ^ 1]);
-    (void)mbar_wait_bounded(&bar[cur], phase[cur]);
+    if (s_tile[cur ^ 1] < a.total_tiles) (void)mbar_wait_bounded(&bar[cur ^ 1], (phases >> (cur ^ 1)) & 1u);
+    (void)mbar_wait_bounded(&bar[cur], (phases >> cur) & 1u);
+  }
+}
+
+const void *stencil_fn(int tile_w, int halo) {
+  if (halo == 2) {
+    switch (tile_w) {
+      case 64: return (const void *)stencil_kernel<64, 2>;
+      case 224: return (const void *)stencil_kernel<224, 2>;
+      default: return (const void *)stencil_kernel<128, 2>;
+    }
+  }
+  switch (tile_w) {
+    case 64: return (const void *)stencil_kernel<64, 0>;
+    case 224: return (const void *)stencil_kernel<224, 0>;
+    default: return (const void *)stencil_kernel<128, 0>;
   }
 }
 
@@ -344,13 +456,16 @@ EncodeTiledFn get_encode() {
 
 }  // namespace
 
+int stencil_tile_width(int requested) {
+  return requested <= 64 ? 64 : (requested <= 128 ? 128 : 224);
+}
+
 size_t stencil_smem_bytes(int tile_h, int tile_w, int halo) {
   const int BW = (tile_w + 2 * halo + 15 + 15) & ~15;
   const int BH = tile_h + 2 * halo;
   const int QP = (tile_w + 2 * halo + 15) & ~15;
-  const int nsq = tile_w + 2 * halo;
   size_t b = (size_t)2 * BH * BW + (size_t)BH * QP + (size_t)tile_h * tile_w;
-  b += (size_t)4 * kMaxNoisePerGroup * ((nsq + 1) & ~1);
+  b += (size_t)4 * kMaxNoisePerGroup * QP;
   b = (b + 7) & ~(size_t)7;
   return b + 2 * sizeof(uint64_t);
 }
@@ -358,19 +473,24 @@ size_t stencil_smem_bytes(int tile_h, int tile_w, int halo) {
 cudaError_t stencil_prepare() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
+    for (int h : {0, 2})
+      for (int w : {64, 128, 224}) {
+        cudaError_t e = cudaFuncSetAttribute(stencil_fn(w, h), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+      }
     attr_set = true;
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-  if (block != kBlock || smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (block != kBlock || smem > 200 * 1024 || stencil_tile_width(a.tile_w) != a.tile_w ||
+      (a.halo != 0 && a.halo != 2))
+    return cudaErrorInvalidValue;
   cudaError_t e = stencil_prepare();
   if (e != cudaSuccess) return e;
-  stencil_kernel<<<grid, block, smem, s>>>(a);
-  return cudaGetLastError();
+  void *args[] = {(void *)&a};
+  return cudaLaunchKernel(stencil_fn(a.tile_w, a.halo), dim3(grid), dim3(block), args, smem, s);
 }
 
 cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t H, int64_t D, int64_t pitch,

@@ -138,6 +138,118 @@ StatusPool &status_pool() {
   return p;
 }
 
+// Workspace of the chain kernel's in-kernel MapReduce finish: one per (device, stream), so launches
+// that may overlap never share a ticket. The ticket starts at 0 and the last CTA resets it.
+struct ChainWs {
+  unsigned long long *partials = nullptr;
+  unsigned int *ticket = nullptr;
+};
+
+mrw_status chain_workspace(int dev, cudaStream_t stream, ChainWs *out) {
+  static std::map<std::pair<int, cudaStream_t>, ChainWs> cache;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_pair(dev, stream);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return MRW_OK;
+  }
+  if (cache.size() >= 256) return fail(MRW_ERR_UNSUPPORTED, "more than 256 streams used for MapReduce");
+  ChainWs w;
+  void *p = nullptr;
+  const size_t bytes = sizeof(unsigned long long) * 3 * kMaxChainGrid + 256;
+  CU(cudaMalloc(&p, bytes));
+  cudaError_t e = cudaMemset(p, 0, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_fail(e, "cudaMemset(workspace)");
+  }
+  w.partials = (unsigned long long *)p;
+  w.ticket = (unsigned int *)((uint8_t *)p + sizeof(unsigned long long) * 3 * kMaxChainGrid);
+  cache[key] = w;
+  *out = w;
+  return MRW_OK;
+}
+
+// Timing-enabled event pairs for futures, reused instead of created per call.
+class EventPool {
+ public:
+  mrw_status take(cudaEvent_t *a, cudaEvent_t *b) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.size() >= 2) {
+      *a = free_.back();
+      free_.pop_back();
+      *b = free_.back();
+      free_.pop_back();
+      return MRW_OK;
+    }
+    if (cudaEventCreate(a) != cudaSuccess) return cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+    if (cudaEventCreate(b) != cudaSuccess) {
+      cudaEventDestroy(*a);
+      return cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+    }
+    return MRW_OK;
+  }
+  void give(cudaEvent_t a, cudaEvent_t b) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.size() < 4096) {
+      if (a) free_.push_back(a);
+      if (b) free_.push_back(b);
+    } else {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<cudaEvent_t> free_;
+};
+EventPool &event_pool() {
+  static EventPool p;
+  return p;
+}
+
+// Ordering-only events (no timing) for overlapped staging, and two side streams per device.
+std::vector<cudaEvent_t> *sync_event_pool() {
+  static std::vector<cudaEvent_t> *pool = new std::vector<cudaEvent_t>();
+  return pool;
+}
+
+mrw_status get_sync_event(cudaEvent_t *e) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!sync_event_pool()->empty()) {
+      *e = sync_event_pool()->back();
+      sync_event_pool()->pop_back();
+      return MRW_OK;
+    }
+  }
+  CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return MRW_OK;
+}
+
+void put_sync_events(std::vector<cudaEvent_t> &v) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (cudaEvent_t e : v) sync_event_pool()->push_back(e);
+  v.clear();
+}
+
+mrw_status side_streams(int dev, cudaStream_t *in, cudaStream_t *out) {
+  static std::map<int, std::pair<cudaStream_t, cudaStream_t>> m;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = m.find(dev);
+  if (it == m.end()) {
+    cudaStream_t a, b;
+    CU(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    it = m.emplace(dev, std::make_pair(a, b)).first;
+  }
+  *in = it->second.first;
+  *out = it->second.second;
+  return MRW_OK;
+}
+
 }  // namespace
 
 // ============================================================================================
@@ -161,6 +273,7 @@ struct mrw_future {
   StatusSlot slot;
   bool has_status = false;
   mrw_status deferred = MRW_OK;  // an error found while enqueueing after the first launch
+  std::vector<cudaEvent_t> sync_events;  // cross-stream ordering events of an overlapped staging
 };
 
 namespace {
@@ -289,8 +402,8 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
         TRY(set_family(p, F_IMAGE));
         if ((int64_t)p.img.size() >= MRW_MAX_STAGES)
           return fail(MRW_ERR_UNSUPPORTED, "more than %d image stages after unrolling loops", MRW_MAX_STAGES);
-        if (n->stage == MRW_ST_THRESHOLD3 && (q.t0 < 0 || q.t0 > 255 || q.t1 < 0 || q.t1 > 255))
-          return fail(MRW_ERR_INVALID_ARG, "threshold outside [0, 255]");
+        if (n->stage == MRW_ST_THRESHOLD3 && (q.t0 < 0 || q.t0 > 255 || q.t1 < 0 || q.t1 > 255 || q.t0 > q.t1))
+          return fail(MRW_ERR_INVALID_ARG, "thresholds must satisfy 0 <= t0 <= t1 <= 255");
         p.img.push_back({ok, q.seed, (uint32_t)(q.t0 & 0xFF) | ((uint32_t)(q.t1 & 0xFF) << 8), q.nu, q.wg});
       } else if (n->stage == MRW_ST_NBODY_ACCEL || n->stage == MRW_ST_NBODY_KDK) {
         TRY(set_family(p, F_NBODY));
@@ -477,7 +590,7 @@ struct Launch {  // everything one execute call enqueues
   int sms;
   std::vector<void *> scratch;  // freed with cudaFreeAsync at the end
   std::vector<Staged> staged;
-  mrw_future *fut = nullptr;
+  std::vector<cudaEvent_t> *events = nullptr;  // ordering events to keep until the work is done
 
   mrw_status alloc(void **p, size_t bytes) {
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, stream);
@@ -637,20 +750,25 @@ struct ChainShape {
   int64_t rows_parallel;
 };
 
-ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, int wg) {
+// Launch shape of a chain group: at most one wave of resident CTAs (the occupancy of the kernel
+// variant caps ctas_per_sm), and grid x block a multiple of the row's 16-byte segments so each
+// thread keeps its column.
+ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, int wg, int n_noise = 0,
+                       bool mirror = false, bool query_occupancy = false) {
   ChainShape s;
   int block = wg ? wg : (cfg.block ? cfg.block : 256);
-  int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
+  int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 64;
   if (block > 256) {  // the chain kernel is compiled for at most 256 threads: keep threads per SM
     cps = std::max(1, cps * block / 256);
     block = 256;
   }
+  s.unroll = cfg.unroll ? cfg.unroll : 4;
+  if (query_occupancy) cps = std::min(cps, chain_blocks_per_sm(n_noise, mirror, s.unroll, block));
   const int64_t col_vecs = (W + 15) / 16;
-  const int64_t target = (int64_t)sms * cps * block;
+  const int64_t target = std::min<int64_t>((int64_t)sms * cps * block, (int64_t)kMaxChainGrid * block);
   s.rows_parallel = std::max<int64_t>(1, std::min<int64_t>(rows, target / col_vecs));
   s.block = block;
   s.grid = (int)((s.rows_parallel * col_vecs + block - 1) / block);
-  s.unroll = cfg.unroll ? cfg.unroll : 4;
   return s;
 }
 
@@ -669,7 +787,15 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
   fill_ops(g.pre, a.mirror, a.ops);
   a.reduce = g.reduce;
   a.red = red;
-  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg);
+  a.row0 = 0;
+  if (g.reduce != RED_NONE) {  // finish the MapReduce in the kernel: no zeroing of `red` needed
+    ChainWs ws;
+    TRY(chain_workspace(L.device, L.stream, &ws));
+    a.partials = ws.partials;
+    a.ticket = ws.ticket;
+  }
+  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true);
+  if (s.grid > kMaxChainGrid) return fail(MRW_ERR_UNSUPPORTED, "chain grid above %d CTAs", kMaxChainGrid);
   a.rows_parallel = s.rows_parallel;
   CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
   return MRW_OK;
@@ -683,8 +809,7 @@ struct StencilShape {
 StencilShape stencil_shape(const mrw_config &cfg, int halo) {
   StencilShape s;
   s.tile_h = cfg.tile_rows ? std::min(cfg.tile_rows, 252 - 2 * halo) : 32;
-  s.tile_w = cfg.tile_cols ? std::min(cfg.tile_cols, 224) : 128;
-  s.tile_w = std::max(16, s.tile_w / 16 * 16);
+  s.tile_w = stencil_tile_width(cfg.tile_cols ? cfg.tile_cols : 128);
   s.tile_h = std::max(1, s.tile_h);
   s.box_w = (int)round_up(s.tile_w + 2 * halo + 15, 16);
   s.box_h = s.tile_h + 2 * halo;
@@ -845,12 +970,84 @@ ImgGeom geom_of(const mrw_buffer &b, const View &v) {
   return g;
 }
 
+// Host buffers, one fused pointwise group: stage the rows in chunks so that the copy-in of chunk
+// c+1, the kernel on chunk c and the copy-out of chunk c-1 overlap (the paper's multi-buffered GPU
+// execution platform, Section 2.2). Each chunk's kernel gets its global first row (Offset trait)
+// and adds its counts into the zeroed result.
+mrw_status enqueue_image_overlapped(Launch &L, const Group &g, const View &vin, const View &vout,
+                                    const View *vred, const ImgGeom &geo, const mrw_config &cfg, int wg) {
+  cudaStream_t s_in, s_out;
+  TRY(side_streams(L.device, &s_in, &s_out));
+  const int64_t pitch = round_up(geo.W, 16);
+  void *din, *dout;
+  TRY(L.alloc(&din, (size_t)(pitch * geo.rows)));
+  TRY(L.alloc(&dout, (size_t)(pitch * geo.rows)));
+  unsigned long long *red = nullptr;
+  void *dred = nullptr;
+  int64_t pred = 0;
+  if (vred) {
+    TRY(resolve(L, *vred, false, true, &dred, &pred));
+    red = (unsigned long long *)dred;
+    CU(cudaMemsetAsync(red, 0, (size_t)(vred->numel() * 8), L.stream));
+  }
+  const int64_t bytes = pitch * geo.rows;
+  const int nch = (int)std::max<int64_t>(2, std::min<int64_t>(16, bytes / (4 << 20)));
+  const int64_t crows = (geo.rows + nch - 1) / nch;
+  cudaEvent_t ev_start;
+  TRY(get_sync_event(&ev_start));
+  L.events->push_back(ev_start);
+  CU(cudaEventRecord(ev_start, L.stream));
+  CU(cudaStreamWaitEvent(s_in, ev_start, 0));
+  CU(cudaStreamWaitEvent(s_out, ev_start, 0));
+  ChainArgs a{};
+  a.W = (int32_t)geo.W;
+  a.col_vecs = (int32_t)((geo.W + 15) / 16);
+  a.nops = (int32_t)g.pre.size();
+  a.mirror = mirror_parity(g.pre);
+  fill_ops(g.pre, a.mirror, a.ops);
+  a.reduce = g.reduce;
+  a.red = red;
+  a.in_pitch = a.out_pitch = pitch;
+  for (int64_t r0 = 0; r0 < geo.rows; r0 += crows) {
+    const int64_t nr = std::min(crows, geo.rows - r0);
+    cudaEvent_t ev_in, ev_k;
+    TRY(get_sync_event(&ev_in));
+    L.events->push_back(ev_in);
+    TRY(get_sync_event(&ev_k));
+    L.events->push_back(ev_k);
+    CU(cudaMemcpy2DAsync((uint8_t *)din + r0 * pitch, pitch, (const uint8_t *)vin.b->data + r0 * vin.pitch, vin.pitch,
+                         geo.W, nr, cudaMemcpyHostToDevice, s_in));
+    CU(cudaEventRecord(ev_in, s_in));
+    CU(cudaStreamWaitEvent(L.stream, ev_in, 0));
+    a.in = (const uint8_t *)din + r0 * pitch;
+    a.out = (uint8_t *)dout + r0 * pitch;
+    a.rows = nr;
+    a.row0 = r0;
+    const ChainShape s = chain_shape(cfg, L.sms, geo.W, nr, wg, count_noise(g.pre), a.mirror != 0, true);
+    a.rows_parallel = s.rows_parallel;
+    CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+    CU(cudaEventRecord(ev_k, L.stream));
+    CU(cudaStreamWaitEvent(s_out, ev_k, 0));
+    CU(cudaMemcpy2DAsync((uint8_t *)vout.b->data + r0 * vout.pitch, vout.pitch, (const uint8_t *)dout + r0 * pitch,
+                         pitch, geo.W, nr, cudaMemcpyDeviceToHost, s_out));
+  }
+  cudaEvent_t ev_done;
+  TRY(get_sync_event(&ev_done));
+  L.events->push_back(ev_done);
+  CU(cudaEventRecord(ev_done, s_out));
+  CU(cudaStreamWaitEvent(L.stream, ev_done, 0));
+  return MRW_OK;
+}
+
 mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
                          unsigned int *status, bool *used_status) {
   View vin, vout, vred;
   TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
   const ImgGeom geo = geom_of(args[0], vin);
   const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
+  if (L.events && gs.size() == 1 && !gs[0].use_stencil && vin.b->memory == MRW_MEM_HOST &&
+      vout.b->memory == MRW_MEM_HOST && geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20))
+    return enqueue_image_overlapped(L, gs[0], vin, vout, p.reduce != RED_NONE ? &vred : nullptr, geo, cfg, p.wg);
   void *din, *dout;
   int64_t pin, pout;
   TRY(resolve(L, vin, true, false, &din, &pin));
@@ -860,8 +1057,7 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
   int64_t pred = 0;
   if (p.reduce != RED_NONE) {
     TRY(resolve(L, vred, false, true, &dred, &pred));
-    red = (unsigned long long *)dred;
-    CU(cudaMemsetAsync(red, 0, (size_t)(vred.numel() * 8), L.stream));
+    red = (unsigned long long *)dred;  // overwritten by the last CTA of the reducing launch
   }
   // intermediates between groups: at most two live at a time
   bool any_stencil = false;
@@ -905,18 +1101,22 @@ struct NbShape {
   int grid, block, bpt;
 };
 
+// Launch shape of the force kernel: `grid` CTAs, each with 4 warp groups of T threads (each group
+// sums a fixed quarter of the j range) and bpt bodies per thread, so a CTA holds T * bpt bodies.
 NbShape nbody_shape(const mrw_config &cfg, int sms, int64_t n, int wg) {
   NbShape s;
+  const int groups = 4;
   s.bpt = (cfg.tile_rows == 1 || cfg.tile_rows == 4) ? cfg.tile_rows : 2;
   const int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 1;
   int64_t grid = std::min<int64_t>((int64_t)sms * cps, std::max<int64_t>(1, (n + 32 * s.bpt - 1) / (32 * s.bpt)));
-  int64_t per = (n + grid - 1) / grid;
-  int64_t block = round_up((per + s.bpt - 1) / s.bpt, 32);
-  if (wg) block = wg;
-  if (block > 256) block = 256;
-  if (block * s.bpt * grid < n) grid = (n + block * s.bpt - 1) / (block * s.bpt);
+  const int64_t per = (n + grid - 1) / grid;
+  int64_t T = round_up((per + s.bpt - 1) / s.bpt, 32);
+  if (wg && wg % (32 * groups) == 0) T = wg / groups;
+  const int64_t tmax = s.bpt == 4 ? 128 : 256;  // the 4-body variant is compiled for 512 threads
+  if (T > tmax) T = tmax;
+  if (T * s.bpt * grid < n) grid = (n + T * s.bpt - 1) / (T * s.bpt);
   s.grid = (int)grid;
-  s.block = (int)block;
+  s.block = (int)(groups * T);
   return s;
 }
 
@@ -1190,8 +1390,8 @@ mrw_status begin_launch(Launch &L, void *stream) {
 
 void free_future(mrw_future *f) {
   if (!f) return;
-  if (f->start) cudaEventDestroy(f->start);
-  if (f->done) cudaEventDestroy(f->done);
+  put_sync_events(f->sync_events);
+  event_pool().give(f->start, f->done);
   status_pool().give(f->slot);
   delete f;
 }
@@ -1312,14 +1512,14 @@ mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, c
   if (!f) return fail(MRW_ERR_OOM, "future");
   f->device = L.device;
   mrw_status s = status_pool().take(&f->slot);
-  if (s == MRW_OK && (cudaEventCreate(&f->start) != cudaSuccess || cudaEventCreate(&f->done) != cudaSuccess))
-    s = cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+  if (s == MRW_OK) s = event_pool().take(&f->start, &f->done);
   if (s != MRW_OK) {
     free_future(f);
     return s;
   }
   cudaEventRecord(f->start, L.stream);
   bool used = false;
+  L.events = &f->sync_events;
   s = enqueue(L, p, args, nargs, c, f->slot.dev, &used);
   if (used) cudaMemcpyAsync(f->slot.host, f->slot.dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, L.stream);
   f->has_status = used;
@@ -1570,8 +1770,7 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
   if (!f) return fail(MRW_ERR_OOM, "future");
   f->device = L.device;
   mrw_status s = status_pool().take(&f->slot);
-  if (s == MRW_OK && (cudaEventCreate(&f->start) != cudaSuccess || cudaEventCreate(&f->done) != cudaSuccess))
-    s = cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+  if (s == MRW_OK) s = event_pool().take(&f->start, &f->done);
   if (s != MRW_OK) {
     free_future(f);
     return s;
@@ -1656,7 +1855,8 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     const int64_t n = args[0].shape[0];
     const NbShape s = nbody_shape(c, sms, n, p.wg);
     o << "{\"family\":\"nbody\",\"n\":" << n << ",\"grid\":" << s.grid << ",\"block\":" << s.block
-      << ",\"bodies_per_thread\":" << s.bpt << ",\"steps\":[";
+      << ",\"j_groups\":4,\"threads_per_group\":" << s.block / 4 << ",\"bodies_per_thread\":" << s.bpt
+      << ",\"steps\":[";
     for (size_t i = 0; i < p.nb.size(); ++i) {
       const NbStep &st = p.nb[i];
       o << (i ? "," : "") << "{\"kind\":\"" << (st.accel ? "accel" : "kdk") << "\",\"iters\":" << st.iters

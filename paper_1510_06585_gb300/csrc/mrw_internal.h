@@ -45,9 +45,21 @@ struct ChainArgs {
   int32_t reduce;          // RedKind
   int32_t pad_;
   unsigned long long *red; // RED_COUNT3: [3] counts; RED_SUM: [1]
+  // MapReduce finish: with `partials` set, every CTA writes its partial result to
+  // partials[3 * blockIdx.x ..] and the last CTA to arrive (ticket) sums them, overwrites `red`
+  // and resets the ticket to 0; with `partials` null, CTAs add into a zeroed `red` atomically
+  // (used when several launches accumulate into one result).
+  unsigned long long *partials;
+  unsigned int *ticket;
+  int64_t row0;            // global row of the first row (the Offset trait, for the noise hash)
   ChainOp ops[kMaxChainOps];
 };
 
+// Largest grid a chain launch may use with an in-kernel MapReduce finish (workspace size).
+constexpr int kMaxChainGrid = 4096;
+
+// Resident CTAs per SM of a chain-kernel variant (occupancy query, cached).
+int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block);
 // n_noise: number of OP_NOISE entries (<= kMaxNoisePerGroup); unroll in {1, 2, 4, 8}.
 cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s);
 
@@ -85,6 +97,8 @@ struct StencilArgs {
   ChainOp suf[kMaxChainOps];
 };
 
+// Tile widths the stencil kernel is compiled for (64, 128, 224): the one a request rounds to.
+int stencil_tile_width(int requested);
 // Shared-memory bytes the stencil kernel needs for a tile shape.
 size_t stencil_smem_bytes(int tile_h, int tile_w, int halo);
 cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s);

@@ -158,7 +158,8 @@ def test_nbody_plan_partitions_satisfy_constraints(lib):
             parts = [tuple(p) for p in d["partitions"]]
             assert partition.check_plan(n, [p for p in parts if p[1] > 0], epu=1, nu=1) == []
             # each CTA's partition fits its threads
-            assert max(p[1] for p in parts) <= d["block"] * d["bodies_per_thread"]
+            assert max(p[1] for p in parts) <= d["threads_per_group"] * d["bodies_per_thread"]
+            assert d["block"] == 4 * d["threads_per_group"] and d["threads_per_group"] % 32 == 0
     u = mrw.plan_describe(tree, _nbody_args(64), mrw.config(fusion=mrw.MRW_FUSE_NONE))
     assert u["steps"][1]["loop"] == "host"
     with pytest.raises(mrw.MrwError):

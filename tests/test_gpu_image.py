@@ -148,3 +148,21 @@ def test_future_elapsed_and_query():
     f.wait(60000)
     assert f.elapsed_ms() > 0
     assert M.load().mrw_future_query(f.h) == M.MRW_OK
+
+
+def test_large_host_buffers_take_the_overlapped_chunked_path():
+    # above 8 MiB the host rows are staged in chunks whose copies overlap the kernels; each chunk's
+    # noise hash uses its global row (Offset trait) and the counts accumulate across chunks
+    img = inputs.filter_image(3000, 3001, seed=12)
+    out = np.zeros_like(img)
+    M.execute(build_image_tree(FILTER, {0: 2}), [img, out]).wait(120000)
+    assert np.array_equal(out, O.filter_pipeline(img, 2))
+    vol = inputs.volume(40, 512, 520, seed=13)
+    pin_in = torch.from_numpy(vol).pin_memory()
+    pin_out = torch.zeros_like(pin_in).pin_memory()
+    counts = torch.full((3,), -1, dtype=torch.int64).pin_memory()
+    seg = M.mapreduce(M.map_(M.stage("threshold3")))
+    for _ in range(2):  # a second call reuses pooled events and streams
+        M.execute(seg, [pin_in, pin_out, counts]).wait(120000)
+        labels_w, counts_w = O.segmentation(vol)
+        assert np.array_equal(pin_out.numpy(), labels_w) and np.array_equal(counts.numpy(), counts_w)
