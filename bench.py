@@ -174,8 +174,10 @@ def time_steps(fn, steps, warmup, world, device, sampler=None):
     if sampler:
         sampler.start()
     e0.record(s)
+    h0 = time.perf_counter()
     for i in range(steps):
         fn(i)
+    time_steps.host_enqueue_us = (time.perf_counter() - h0) / max(steps, 1) * 1e6
     e1.record(s)
     torch.cuda.synchronize()
     if sampler:
@@ -183,6 +185,19 @@ def time_steps(fn, steps, warmup, world, device, sampler=None):
     barrier(world)
     torch.cuda.synchronize()
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device)
+
+
+def tune_candidates(M, tree, args, reps=5):
+    """Time the 16 candidate configurations; return (best fused, best kernel-per-stage, summary)."""
+    cfgs = M.tune_candidates(tree, args)
+    t = M.tune_measure(tree, args, cfgs, reps=reps)
+    fused = [i for i in range(len(cfgs)) if cfgs[i].fusion == M.MRW_FUSE_ALL and t[i] > 0]
+    unfused = [i for i in range(len(cfgs)) if cfgs[i].fusion == M.MRW_FUSE_NONE and t[i] > 0]
+    bf = min(fused, key=lambda i: t[i])
+    bu = min(unfused, key=lambda i: t[i])
+    return cfgs[bf], cfgs[bu], {"fused_index": bf, "fused_cfg": list(cfgs[bf].as_tuple()),
+                                "unfused_index": bu, "default_ms": round(float(t[0]), 5),
+                                "best_ms": round(float(t[bf]), 5), "candidates": 16}
 
 
 def run_mrw(args):
@@ -210,7 +225,7 @@ def run_mrw(args):
             pending.clear()
 
         out = extras(M, lib, device, world, torch.cuda.current_stream().cuda_stream, peaks, pending, drain_only,
-                     set(args.workloads.split(",")), args.batch_n)
+                     set(args.workloads.split(",")), args.batch_n, args.filter_sides)
         if rank == 0:
             print(json.dumps({"workloads": out}), flush=True)
         return
@@ -227,8 +242,6 @@ def run_mrw(args):
     lib = M.load()
     bufs = [M.buffers(*s) for s in sets]
     stream = torch.cuda.current_stream().cuda_stream
-    fused_cfg = M.config()
-    unfused_cfg = M.config(fusion=M.MRW_FUSE_NONE)
 
     # futures are released after the timed region (releasing one waits for its work)
     pending = []
@@ -247,8 +260,12 @@ def run_mrw(args):
             M.check(s, "future")
         pending.clear()
 
+    # the executor's autotuner picks the launch configuration (all 16 candidates timed on these
+    # buffers); the kernel-per-stage baseline gets the best of its own 8 candidates
+    fused_cfg, unfused_cfg, tuning = tune_candidates(M, tree, list(sets[0]))
     sampler = ClockSampler(local)
     t_fused = time_steps(step_async(fused_cfg), K, W, world, device, sampler)
+    host_enqueue_us = time_steps.host_enqueue_us  # host time to enqueue one step (no GPU wait inside)
     drain()
     # correctness of what was timed
     hist = np.bincount(np.digitize(vol.reshape(-1), [85, 170]), minlength=3).astype(np.int64)
@@ -282,7 +299,8 @@ def run_mrw(args):
         "ms_per_step": round(fused_s * 1e3, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8", "data": "synthetic (seeded 3-component mixture volume)",
         "config": {"workload": WORKLOAD, "shape": list(SEG_SHAPE), "l2": "2 rotating input/output sets, 512 MiB > 2x L2",
-                   "parallelism": f"replicas x{world}", "launch": "fused chain kernel, default config"},
+                   "parallelism": f"replicas x{world}", "launch": "fused chain kernel, autotuned config",
+                   "tuned": tuning},
         "kernel_per_stage": {"value": round(world * SEG_BYTES * K / t_unfused / 1e9, 2), "unit": "GB/s",
                              "ms_per_step": round(unfused_s * 1e3, 5),
                              "speedup_fused": round(unfused_s / fused_s, 3)},
@@ -294,13 +312,14 @@ def run_mrw(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
                 "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e},
         "gpu_launches": K,
+        "host_enqueue_us_per_step": round(host_enqueue_us, 2),
         "clocks": sampler.summary(),
     }
 
     # ---------------- other workloads of the hot path ----------------
     if args.extras:
         result["workloads"] = extras(M, lib, device, world, stream, peaks, pending, drain,
-                                     set(args.workloads.split(",")), args.batch_n)
+                                     set(args.workloads.split(",")), args.batch_n, args.filter_sides)
 
     # ---------------- CPU baseline (oracle) ----------------
     if rank == 0 and world == 1:
@@ -312,7 +331,27 @@ def run_mrw(args):
         dist.destroy_process_group()
 
 
-def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n):
+def tune_candidates_buffers(M, tree, bufarr, reps=5):
+    """tune_candidates on a prepared mrw_buffer array."""
+    lib = M.load()
+    n = len(bufarr)
+    cnt = ctypes.c_int32()
+    M.check(lib.mrw_tune_candidates(tree.h, bufarr, n, None, 0, ctypes.byref(cnt)), "candidates")
+    cfgs = (M.mrw_config * cnt.value)()
+    M.check(lib.mrw_tune_candidates(tree.h, bufarr, n, cfgs, cnt.value, ctypes.byref(cnt)), "candidates")
+    t = (ctypes.c_float * cnt.value)()
+    M.check(lib.mrw_tune_measure(tree.h, bufarr, n, cfgs, cnt.value, reps,
+                                 M.stream_handle(), t), "measure")
+    t = np.array(t[:])
+    fused = [i for i in range(cnt.value) if cfgs[i].fusion == M.MRW_FUSE_ALL and t[i] > 0]
+    unfused = [i for i in range(cnt.value) if cfgs[i].fusion == M.MRW_FUSE_NONE and t[i] > 0]
+    bf = min(fused, key=lambda i: t[i])
+    bu = min(unfused, key=lambda i: t[i])
+    return cfgs[bf], cfgs[bu], {"fused_index": bf, "fused_cfg": list(cfgs[bf].as_tuple()), "unfused_index": bu,
+                                "default_ms": round(float(t[0]), 5), "best_ms": round(float(t[bf]), 5)}
+
+
+def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n, filter_sides="1024,8192"):
     import torch
 
     from paper_1510_06585_gb300 import inputs
@@ -343,17 +382,19 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n)
     fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
     # Filter Pipeline (noise -> solarise -> mirror)
     ftree = M.pipeline(M.stage("noise", seed=2), M.stage("solarise"), M.stage("mirror"))
-    for side, nsets in (((1024, 1), (8192, 2)) if "filter" in which else ()):
+    sides = [int(v) for v in filter_sides.split(",") if v] if "filter" in which else []
+    for side, nsets in ((v, 1 if v <= 2048 else 2) for v in sides):
         img = inputs.filter_image(side, side)
         sets = []
         for _ in range(nsets):
             x = torch.from_numpy(img).to(device)
             sets.append(M.buffers(x, torch.empty_like(x)))
         reps = 200 if side == 1024 else 20
-        tf = timed(launcher(ftree, sets, fused), reps)
-        tu = timed(launcher(ftree, sets, unfused), reps)
+        f_cfg, u_cfg, tinfo = tune_candidates_buffers(M, ftree, sets[0])
+        tf = timed(launcher(ftree, sets, f_cfg), reps)
+        tu = timed(launcher(ftree, sets, u_cfg), reps)
         b = 2 * side * side
-        out[f"filter_{side}"] = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2),
+        out[f"filter_{side}"] = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2), "tuned": tinfo,
                                  "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
                                  "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
                                  "l2": "resident (2 MiB)" if side == 1024 else "2 rotating sets, 256 MiB"}
@@ -413,12 +454,19 @@ def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stre
         return f
 
     px = float((shapes[:, 0] * shapes[:, 1]).sum())
-    tb = timed(blaunch(fused), 5)
-    tbu = timed(blaunch(unfused), 3)
+    # autotune the batched launch over the candidate tile shapes (fused and kernel-per-stage)
+    cand = M.tune_candidates(btree, [bx[:64].view(8, 8), by[:64].view(8, 8)])
+    times = [timed(blaunch(c), 2, warm=1) for c in cand]
+    bf = min(range(8), key=lambda i: times[i])
+    bu = min(range(8, 16), key=lambda i: times[i])
+    tb = timed(blaunch(cand[bf]), 5)
+    tbu = timed(blaunch(cand[bu]), 3)
     out[f"batched_{batch_n}"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
                            "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
                            "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
-                           "launches_per_step": 1}
+                           "launches_per_step": 1, "tuned": {"fused_index": bf, "fused_cfg": list(cand[bf].as_tuple()),
+                                                             "unfused_index": bu,
+                                                             "default_ms": round(times[0] * 1e3, 4)}}
     return out
 
 
@@ -474,6 +522,7 @@ def main():
     ap.add_argument("--workloads", default="filter,nbody,batched",
                     help="comma list of the extra workloads to run (filter, nbody, batched)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
+    ap.add_argument("--filter-sides", default="1024,8192", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
                     help="skip the headline timing (profiling runs of one extra workload)")
     args = ap.parse_args()

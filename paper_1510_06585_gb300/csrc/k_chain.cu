@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
   uint32_t cnt_ge0 = 0, cnt_ge1 = 0, cnt_n = 0;
   unsigned long long vsum = 0;
 
+  // let the next kernel on the stream be scheduled as soon as SM resources free up
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (gid >= nthreads) asm volatile("griddepcontrol.wait;" ::: "memory");
   if (gid < nthreads) {
     const int col = (int)(gid % a.col_vecs);
     const int64_t r0 = gid / a.col_vecs;
@@ -193,6 +196,9 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
         ++kn;
       }
     }
+    // Programmatic dependent launch: everything above reads only kernel parameters, so it may run
+    // while the previous kernel on the stream drains; global memory is touched only after it ends.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // valid-byte masks of this thread's segment (all ones unless it is the row's ragged tail)
     uint32_t vmask[4];
 #pragma unroll
@@ -305,40 +311,25 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
       t[1] += red_smem[i][1];
       t[2] += red_smem[i][2];
     }
-    if (a.partials == nullptr) {
-      for (int k = 0; k < nout; ++k)
-        if (t[k]) atomicAdd(a.red + k, t[k]);
-      is_last = false;
-    } else {
-      for (int k = 0; k < 3; ++k) a.partials[3 * blockIdx.x + k] = t[k];
+    // with a workspace: add into its accumulator (left at zero by the previous launch), and let
+    // the last CTA to arrive move the totals into `red`; without: add into a zeroed `red`
+    unsigned long long *dst = a.partials ? a.partials : a.red;
+    for (int k = 0; k < nout; ++k)
+      if (t[k]) atomicAdd(dst + k, t[k]);
+    is_last = false;
+    if (a.partials) {
       __threadfence();
       is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
   }
   __syncthreads();
-  if (!is_last) return;
-  // last CTA: sum every CTA's partial result (integer sums: any order gives the same value)
+  if (!is_last || threadIdx.x != 0) return;
   __threadfence();
-  unsigned long long t[3] = {0, 0, 0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-    for (int k = 0; k < 3; ++k) t[k] += __ldcg(a.partials + 3 * b + k);
-  for (int k = 0; k < 3; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xFFFFFFFFu, t[k], o);
+  for (int k = 0; k < nout; ++k) {
+    a.red[k] = __ldcg(a.partials + k);
+    a.partials[k] = 0ull;  // clean for the next launch on this workspace
   }
-  __syncthreads();  // red_smem is reused
-  if (lane == 0)
-    for (int k = 0; k < 3; ++k) red_smem[warp][k] = t[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int k = 0; k < nout; ++k) {
-      unsigned long long v = 0;
-      for (int i = 0; i < nw; ++i) v += red_smem[i][k];
-      a.red[k] = v;
-    }
-    *a.ticket = 0u;  // ready for the next launch on this workspace
-  }
+  *a.ticket = 0u;
 }
 
 template <int NN, bool MIR, int U>
@@ -388,8 +379,18 @@ cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, 
   if (grid <= 0) return cudaSuccess;
   const void *fn = pick(n_noise, a.mirror != 0, unroll);
   if (!fn) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   void *args[] = {(void *)&a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace mrw

@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
   uint32_t *qcol = reinterpret_cast<uint32_t *>(rt + TH * TW);  // [kMaxNoisePerGroup][QP]
   uint64_t *bar = reinterpret_cast<uint64_t *>(qcol + kMaxNoisePerGroup * QP);
   __shared__ int64_t s_tile[2];
+  __shared__ Tile s_geo[2];  // geometry of the tile in each buffer, computed once by thread 0
   __shared__ int s_fail;
 
   const int tid = threadIdx.x;
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
     s_tile[0] = t;
     if (t < a.total_tiles) {
       const Tile g = locate(a, t);
+      s_geo[0] = g;
       mbar_expect_tx(&bar[0], box_bytes);
       tma_load_3d(smem, a.maps + g.inst, g.bx, g.by, g.z, &bar[0]);
     }
@@ -263,8 +265,10 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
   while (true) {
     const int64_t t = s_tile[cur];
     if (t >= a.total_tiles) break;
-    const Tile g = locate(a, t);
-    const StencilInstance inst = a.inst[g.inst];
+    const Tile g = s_geo[cur];
+    const int64_t out_off = a.inst[g.inst].out_off;
+    const int32_t pitch_out = a.inst[g.inst].pitch_out;
+    const uint32_t seed_xor = a.inst[g.inst].seed_xor;
 
     // Prefetch the next tile into the other buffer (free since the end of the previous iteration).
     if (tid == 0) {
@@ -272,6 +276,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
       s_tile[cur ^ 1] = tn;
       if (tn < a.total_tiles) {
         const Tile gn = locate(a, tn);
+        s_geo[cur ^ 1] = gn;
         fence_proxy_async();
         mbar_expect_tx(&bar[cur ^ 1], box_bytes);
         tma_load_3d(smem + (cur ^ 1) * BH * BW, a.maps + gn.inst, gn.bx, gn.by, gn.z, &bar[cur ^ 1]);
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
       int kn = 0;
       for (int i = 0; i < a.npre && kn < kMaxNoisePerGroup; ++i) {
         if (a.pre[i].kind != OP_NOISE) continue;
-        const uint32_t fs = fmix32(a.pre[i].seed ^ inst.seed_xor);
+        const uint32_t fs = fmix32(a.pre[i].seed ^ seed_xor);
         const int flip = a.pre[i].flip;
         for (int j = tid; j < 4 * QW4; j += kBlock) {
           const int gc = min(max(g.r0 - H + j, 0), g.W - 1);
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
 
     const uint8_t *bx = smem + cur * BH * BW;
     const uint32_t plane_row0 = (uint32_t)g.z * (uint32_t)g.H;
-    uint8_t *obase = a.out_base + inst.out_off + ((int64_t)g.z * g.H + g.y0) * inst.pitch_out + g.x0;
+    uint8_t *obase = a.out_base + out_off + ((int64_t)g.z * g.H + g.y0) * pitch_out + g.x0;
 
     // Phase A: Q words (prefix applied to the clamped neighbourhood), 4 columns per task.
     const int qrows = g.rows + 2 * H;
@@ -314,11 +319,11 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
       const int gy = min(max(g.y0 - H + i, 0), g.H - 1);
       const uint8_t *brow = bx + (gy - g.by) * BW;
       const int c0 = g.r0 - H + 4 * jq;
-      Cols4 gc;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) gc.c[k] = min(max(c0 + k, 0), g.W - 1);
+      Cols4 gc;  // clamped (edge-replicated) columns of the quad
       uint32_t w;
       if (c0 >= 0 && c0 + 3 <= g.W - 1 && 4 * jq + 4 <= qcols) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gc.c[k] = c0 + k;
         // a whole quad inside the image and inside the tile's Q range: one (funnel-shifted) word
         if (!a.mpre) {
           w = load4(brow, c0 - g.bx);
@@ -328,6 +333,8 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
       } else {
         // image edges (replicated columns) and the tile's ragged last quad
         w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gc.c[k] = min(max(c0 + k, 0), g.W - 1);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (4 * jq + k < qcols) {
@@ -339,9 +346,9 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
       const uint32_t y = plane_row0 + (uint32_t)gy;
       const uint4 cp0 = *reinterpret_cast<const uint4 *>(qcol + 4 * jq);
       const uint4 cp1 = *reinterpret_cast<const uint4 *>(qcol + QP + 4 * jq);
-      w = apply_ops_word(a.pre, a.npre, w, cp0, cp1, y ^ (y >> 16), gc, g.W, inst.seed_xor);
+      w = apply_ops_word(a.pre, a.npre, w, cp0, cp1, y ^ (y >> 16), gc, g.W, seed_xor);
       if (H == 0 && direct) {
-        store4(obase + (int64_t)i * inst.pitch_out + 4 * jq, w, min(4, g.cols - 4 * jq));
+        store4(obase + (int64_t)i * pitch_out + 4 * jq, w, min(4, g.cols - 4 * jq));
       } else {
         *reinterpret_cast<uint32_t *>(qt + i * QP + 4 * jq) = w;
       }
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
                 const uint32_t o = ((s02 & 0xFFFFu) + 12u) / 25u | ((((s13 & 0xFFFFu) + 12u) / 25u) << 8) |
                                    ((((s02 >> 16) + 12u) / 25u) << 16) | ((((s13 >> 16) + 12u) / 25u) << 24);
                 if (direct) {
-                  store4(obase + (int64_t)r * inst.pitch_out + 4 * jr, o, min(4, g.cols - 4 * jr));
+                  store4(obase + (int64_t)r * pitch_out + 4 * jr, o, min(4, g.cols - 4 * jr));
                 } else {
                   *reinterpret_cast<uint32_t *>(rt + r * TW + 4 * jr) = o;
                 }
@@ -402,10 +409,10 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
           const int nv = min(16, g.cols - 16 * c);
           const uint8_t *rrow = rsrc + i * rpitch;
           const uint32_t y = plane_row0 + (uint32_t)(g.y0 + i);
-          uint8_t *orow = obase + (int64_t)i * inst.pitch_out + 16 * c;
+          uint8_t *orow = obase + (int64_t)i * pitch_out + 16 * c;
           for (int k = 0; k < nv; ++k) {
             const int lc = a.msuf ? g.cols - 1 - 16 * c - k : 16 * c + k;
-            orow[k] = (uint8_t)apply_ops_px(a.suf, a.nsuf, rrow[lc], g.x0 + 16 * c + k, g.W, y, inst.seed_xor);
+            orow[k] = (uint8_t)apply_ops_px(a.suf, a.nsuf, rrow[lc], g.x0 + 16 * c + k, g.W, y, seed_xor);
           }
         }
       }

@@ -45,9 +45,9 @@ struct ChainArgs {
   int32_t reduce;          // RedKind
   int32_t pad_;
   unsigned long long *red; // RED_COUNT3: [3] counts; RED_SUM: [1]
-  // MapReduce finish: with `partials` set, every CTA writes its partial result to
-  // partials[3 * blockIdx.x ..] and the last CTA to arrive (ticket) sums them, overwrites `red`
-  // and resets the ticket to 0; with `partials` null, CTAs add into a zeroed `red` atomically
+  // MapReduce finish: with `partials` set (a per-stream workspace whose 3 accumulators and ticket
+  // are zero between launches), CTAs add into the accumulators and the last CTA to arrive (ticket)
+  // moves them into `red` and zeroes them again; with `partials` null, CTAs add into a zeroed `red`
   // (used when several launches accumulate into one result).
   unsigned long long *partials;
   unsigned int *ticket;
