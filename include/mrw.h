@@ -128,9 +128,15 @@ typedef struct mrw_stage_params {
 typedef enum mrw_reduce_op { MRW_RED_ADD = 0, MRW_RED_SUB = 1, MRW_RED_MUL = 2, MRW_RED_DIV = 3 } mrw_reduce_op;
 
 /* Loop state (Section 2.1: stop condition, carried data, global synchronisation). The device
- * evaluates the condition: for MRW_LOOP_FOR the body runs max_iters times; the iteration counter
- * lives in device memory and the loop is a CUDA graph whose conditional node re-reads it. */
-typedef enum mrw_loop_kind { MRW_LOOP_FOR = 0 } mrw_loop_kind;
+ * evaluates the condition:
+ *   MRW_LOOP_FOR: the body runs max_iters times; the iteration counter lives in device memory and
+ *     an N-body loop is a CUDA graph whose conditional node re-reads it;
+ *   MRW_LOOP_WHILE_CHANGED (image trees): the body runs again while its last run changed its input
+ *     anywhere, at most max_iters times (a convergence loop, e.g. blurring to a fixed point). A
+ *     device kernel compares each result with its input and sets the condition of a conditional
+ *     WHILE node, so the number of iterations is decided on the GPU. At most one such loop per
+ *     tree, not inside a MapReduce. */
+typedef enum mrw_loop_kind { MRW_LOOP_FOR = 0, MRW_LOOP_WHILE_CHANGED = 1 } mrw_loop_kind;
 typedef struct mrw_loop_state {
   int64_t max_iters;   /* 0 .. 1e8                                                              */
   int32_t kind;        /* mrw_loop_kind                                                         */

@@ -18,6 +18,8 @@ Trees are plain tuples:
     ("mapreduce", child, op)    op = "add" (the only merging function the executor's
                                 device path implements)
     ("loop", child, iters)
+    ("loop_while", child, max_iters) repeat while the last run changed its input (at most
+                                max_iters runs): a convergence loop on image trees
 
 Every intermediate is materialised; ``trace`` records the leaves in the order
 they ran. Parity is pinned by tests/test_oracle_skeleton.py (stage order with
@@ -66,6 +68,14 @@ def evaluate_image(tree, img: np.ndarray, trace: list | None = None, y0: int = 0
             img, r = evaluate_image(tree[1], img, trace, y0)
             red = r if r is not None else red
         return img, red
+    if kind == "loop_while":
+        for _ in range(int(tree[2])):
+            out, _ = evaluate_image(tree[1], img, trace, y0)
+            changed = not np.array_equal(out, img)
+            img = out
+            if not changed:
+                break
+        return img, None
     raise ValueError(f"unknown node {kind!r}")
 
 

@@ -387,8 +387,10 @@ cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;  // plain edges inside captured graphs
   void *args[] = {(void *)&a};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }

@@ -363,6 +363,9 @@ struct Program {
   std::vector<NbStep> nb;
   std::vector<float> alphas;
   int nu = 0, wg = 0;
+  // a WHILE_CHANGED loop over img[while_begin, while_end), at most while_max runs (-1: none)
+  int while_begin = -1, while_end = -1;
+  int64_t while_max = 0;
 };
 
 mrw_status set_family(Program &p, Family f) {
@@ -449,7 +452,22 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
     case N_LOOP: {
       const mrw_loop_state &st = n->loop;
       if (st.max_iters < 0 || st.max_iters > 100000000) return fail(MRW_ERR_INVALID_ARG, "loop max_iters out of range");
-      if (st.kind != MRW_LOOP_FOR) return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", st.kind);
+      if (st.kind != MRW_LOOP_FOR && st.kind != MRW_LOOP_WHILE_CHANGED)
+        return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", st.kind);
+      if (st.kind == MRW_LOOP_WHILE_CHANGED) {
+        if (p.while_begin >= 0) return fail(MRW_ERR_UNSUPPORTED, "more than one WHILE_CHANGED loop in a tree");
+        if (loop_mult > 1) return fail(MRW_ERR_UNSUPPORTED, "a WHILE_CHANGED loop inside another loop");
+        Program probe;
+        TRY(flatten(n->kids[0], probe, depth + 1, false, 1));
+        if (probe.fam != F_IMAGE || probe.while_begin >= 0)
+          return fail(MRW_ERR_UNSUPPORTED, "WHILE_CHANGED loops run image trees");
+        TRY(set_family(p, F_IMAGE));
+        p.while_begin = (int)p.img.size();
+        TRY(flatten(n->kids[0], p, depth + 1, false, 1));
+        p.while_end = (int)p.img.size();
+        p.while_max = st.max_iters;
+        return MRW_OK;
+      }
       if (st.max_iters == 0) return MRW_OK;
       if (loop_mult > 1 && st.max_iters > 1)
         return fail(MRW_ERR_UNSUPPORTED, "nested loops with more than one iteration each");
@@ -970,6 +988,43 @@ ImgGeom geom_of(const mrw_buffer &b, const View &v) {
   return g;
 }
 
+// Run `gs` from src to dst: groups in order, intermediates in (at most two) stream-ordered
+// scratch images; a reduce-only group reads the previous group's output.
+mrw_status run_groups(Launch &L, const std::vector<Group> &gs, const uint8_t *src, int64_t sp, uint8_t *dst,
+                      int64_t dp_final, const ImgGeom &geo, const mrw_config &cfg, int wg, unsigned int *status,
+                      bool *used_status, unsigned long long *red) {
+  bool any_stencil = false;
+  for (const Group &g : gs) any_stencil |= g.use_stencil;
+  if (any_stencil && status) CU(cudaMemsetAsync(status, 0, sizeof(unsigned int), L.stream));
+  const int64_t tpitch = round_up(geo.W, 16);
+  void *tmp[2] = {nullptr, nullptr};
+  int n_out_groups = 0;
+  for (const Group &g : gs) n_out_groups += !g.reduce_only;
+  if (n_out_groups > 1) TRY(L.alloc(&tmp[0], (size_t)(tpitch * geo.rows)));
+  if (n_out_groups > 2) TRY(L.alloc(&tmp[1], (size_t)(tpitch * geo.rows)));
+  int k = 0;
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const Group &g = gs[gi];
+    if (g.reduce_only) {
+      TRY(run_chain(L, g, src, sp, nullptr, 0, geo, cfg, wg, red));
+      continue;
+    }
+    ++k;
+    const bool last = k == n_out_groups;
+    uint8_t *d = last ? dst : (uint8_t *)tmp[(k - 1) & 1];
+    const int64_t dp = last ? dp_final : tpitch;
+    if (g.use_stencil) {
+      TRY(run_stencil_single(L, g, src, sp, d, dp, geo, cfg, status));
+      *used_status = true;
+    } else {
+      TRY(run_chain(L, g, src, sp, d, dp, geo, cfg, wg, g.reduce != RED_NONE ? red : nullptr));
+    }
+    src = d;
+    sp = dp;
+  }
+  return MRW_OK;
+}
+
 // Host buffers, one fused pointwise group: stage the rows in chunks so that the copy-in of chunk
 // c+1, the kernel on chunk c and the copy-out of chunk c-1 overlap (the paper's multi-buffered GPU
 // execution platform, Section 2.2). Each chunk's kernel gets its global first row (Offset trait)
@@ -1039,11 +1094,264 @@ mrw_status enqueue_image_overlapped(Launch &L, const Group &g, const View &vin, 
   return MRW_OK;
 }
 
+// ============================================================================================
+// WHILE_CHANGED loops: a cached CUDA graph {init; WHILE(cond) { body groups A -> B; a := b where
+// they differ, flag; count, set cond }} whose condition is evaluated on the device
+// ============================================================================================
+Program sub_program(const Program &p, int b, int e) {
+  Program q;
+  q.fam = F_IMAGE;
+  q.img.assign(p.img.begin() + b, p.img.begin() + e);
+  q.nu = p.nu;
+  q.wg = p.wg;
+  q.has_map = p.has_map;
+  return q;
+}
+
+struct Prepared {
+  bool stencil = false;
+  ChainArgs ca{};
+  ChainShape cs{};
+  int n_noise = 0;
+  StencilArgs sa{};
+  int grid = 0;
+  size_t smem = 0;
+  unsigned int *queue = nullptr;
+};
+
+struct WhilePlan {
+  void *mem = nullptr, *small = nullptr;
+  uint8_t *A = nullptr, *B = nullptr;
+  int64_t pitch = 0;
+  LoopCtrl *ctrl = nullptr;
+  unsigned int *words = nullptr;  // [0] changed, [1] status, [2 ..] tile queues
+  std::vector<void *> owned;
+  cudaGraphExec_t exec = nullptr;
+};
+
+std::map<std::string, WhilePlan> &while_plans() {
+  static std::map<std::string, WhilePlan> m;
+  return m;
+}
+
+void destroy_while_plan(WhilePlan &w) {
+  if (w.exec) cudaGraphExecDestroy(w.exec);
+  for (void *p : w.owned) cudaFree(p);
+  if (w.mem) cudaFree(w.mem);
+  if (w.small) cudaFree(w.small);
+}
+
+// Stencil launch with its tables in plan-owned memory (uploaded now, outside any capture).
+mrw_status prepare_stencil(Launch &L, const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op,
+                           const ImgGeom &geo, const mrw_config &cfg, unsigned int *status, unsigned int *queue,
+                           std::vector<void *> *owned, Prepared *pr) {
+  StencilArgs a{};
+  fill_stencil_ops(g, a);
+  const StencilShape s = stencil_shape(cfg, a.halo);
+  StencilTables t;
+  t.maps.resize(1);
+  CU(encode_u8_map(&t.maps[0], in, geo.W, geo.H, geo.D, ip, s.box_w, s.box_h));
+  StencilInstance inst{};
+  inst.W = (int32_t)geo.W;
+  inst.H = (int32_t)geo.H;
+  inst.D = (int32_t)geo.D;
+  inst.pitch_in = (int32_t)ip;
+  inst.pitch_out = (int32_t)op;
+  inst.tiles_x = (int32_t)((geo.W + s.tile_w - 1) / s.tile_w);
+  inst.tiles_y = (int32_t)((geo.H + s.tile_h - 1) / s.tile_h);
+  t.inst.push_back(inst);
+  t.total = (int64_t)inst.tiles_x * inst.tiles_y * geo.D;
+  t.prefix = {0, t.total};
+  void *dm, *di, *dp;
+  TRY(upload_tables(L, t, &dm, &di, &dp, true, owned));
+  a.maps = (const CUtensorMap *)dm;
+  a.inst = (const StencilInstance *)di;
+  a.tile_prefix = (const int64_t *)dp;
+  a.in_base = in;
+  a.out_base = out;
+  a.queue = queue;
+  a.status = status;
+  a.total_tiles = t.total;
+  a.ninst = 1;
+  a.tile_h = s.tile_h;
+  a.tile_w = s.tile_w;
+  a.box_w = s.box_w;
+  a.box_h = s.box_h;
+  pr->stencil = true;
+  pr->sa = a;
+  pr->grid = (int)std::max<int64_t>(1, std::min<int64_t>(t.total, (int64_t)L.sms * s.cps));
+  pr->smem = s.smem;
+  pr->queue = queue;
+  return MRW_OK;
+}
+
+void prepare_chain(const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op, const ImgGeom &geo,
+                   const mrw_config &cfg, int sms, int wg, Prepared *pr) {
+  ChainArgs &a = pr->ca;
+  a = ChainArgs{};
+  a.in = in;
+  a.out = out;
+  a.in_pitch = ip;
+  a.out_pitch = op;
+  a.rows = geo.rows;
+  a.W = (int32_t)geo.W;
+  a.col_vecs = (int32_t)((geo.W + 15) / 16);
+  a.nops = (int32_t)g.pre.size();
+  a.mirror = mirror_parity(g.pre);
+  fill_ops(g.pre, a.mirror, a.ops);
+  pr->n_noise = count_noise(g.pre);
+  pr->cs = chain_shape(cfg, sms, geo.W, geo.rows, wg, pr->n_noise, a.mirror != 0, true);
+  a.rows_parallel = pr->cs.rows_parallel;
+}
+
+mrw_status build_while_plan(Launch &L, const Program &p, const ImgGeom &geo, const mrw_config &cfg, WhilePlan *wp) {
+  const int64_t P = round_up(geo.W, 16), bytes = P * geo.rows;
+  const Program body = sub_program(p, p.while_begin, p.while_end);
+  const std::vector<Group> gs = group_stages(body, cfg.fusion == MRW_FUSE_ALL, false);
+  if (gs.size() > 32) return fail(MRW_ERR_UNSUPPORTED, "loop body with more than 32 kernels");
+  CU(cudaMalloc(&wp->mem, (size_t)(4 * bytes)));
+  CU(cudaMalloc(&wp->small, 4096));
+  CU(cudaMemset(wp->small, 0, 4096));
+  wp->pitch = P;
+  wp->A = (uint8_t *)wp->mem;
+  wp->B = wp->A + bytes;
+  uint8_t *T[2] = {wp->B + bytes, wp->B + 2 * bytes};
+  wp->ctrl = (LoopCtrl *)wp->small;
+  wp->words = (unsigned int *)((uint8_t *)wp->small + 256);
+  std::vector<Prepared> prep(gs.size());
+  const uint8_t *src = wp->A;
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const bool last = gi + 1 == gs.size();
+    uint8_t *dst = last ? wp->B : T[gi & 1];
+    if (gs[gi].use_stencil) {
+      TRY(prepare_stencil(L, gs[gi], src, P, dst, P, geo, cfg, wp->words + 1, wp->words + 2 + gi, &wp->owned,
+                          &prep[gi]));
+    } else {
+      prepare_chain(gs[gi], src, P, dst, P, geo, cfg, L.sms, p.wg, &prep[gi]);
+    }
+    src = dst;
+  }
+  CU(stencil_prepare());
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  // init: reset the counter, the changed flag and the status word
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = launch_while_init(wp->ctrl, wp->words, (unsigned long long)p.while_max, cs);
+    cudaGraph_t g2 = nullptr;
+    e = cudaStreamEndCapture(cs, &g2);
+    if (e == cudaSuccess) e = e1;
+  }
+  cudaGraphNode_t init_node = nullptr;
+  size_t nn = 1;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &init_node, &nn);
+  cudaGraphConditionalHandle handle{};
+  cudaGraph_t bodyg = nullptr;
+  if (e == cudaSuccess)
+    e = cudaGraphConditionalHandleCreate(&handle, graph, p.while_max > 0 ? 1u : 0u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond_node;
+    e = cudaGraphAddNode(&cond_node, graph, &init_node, nullptr, 1, &cp);
+    if (e == cudaSuccess) bodyg = cp.conditional.phGraph_out[0];
+  }
+  // body: the groups A -> B, then a := b where changed, then the control kernel
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaSuccess;
+    for (size_t gi = 0; e1 == cudaSuccess && gi < prep.size(); ++gi) {
+      const Prepared &pr = prep[gi];
+      if (pr.stencil) {
+        e1 = cudaMemsetAsync(pr.queue, 0, sizeof(unsigned int), cs);
+        if (e1 == cudaSuccess) e1 = launch_stencil(pr.sa, pr.grid, 256, pr.smem, cs);
+      } else {
+        e1 = launch_chain(pr.ca, pr.n_noise, pr.cs.unroll, pr.cs.grid, pr.cs.block, cs);
+      }
+    }
+    if (e1 == cudaSuccess) e1 = launch_compare_copy(wp->B, wp->A, geo.rows, (int32_t)geo.W, P, wp->words, L.sms, cs);
+    if (e1 == cudaSuccess) e1 = launch_while_control(wp->ctrl, wp->words, handle, cs);
+    cudaGraph_t g3 = nullptr;
+    e = cudaStreamEndCapture(cs, &g3);
+    if (e == cudaSuccess) e = e1;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&wp->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "building the WHILE_CHANGED loop graph");
+  return MRW_OK;
+}
+
+std::string image_program_key(const Program &p, const ImgGeom &geo, const mrw_config &c, int dev, cudaStream_t st) {
+  std::ostringstream o;
+  o << dev << "|" << (void *)st << "|" << geo.W << "x" << geo.H << "x" << geo.D << "|" << p.while_begin << ","
+    << p.while_end << "," << p.while_max << "|" << c.fusion << "," << c.block << "," << c.ctas_per_sm << ","
+    << c.tile_rows << "," << c.tile_cols << "," << c.unroll << "|";
+  for (const ImgStage &s : p.img) o << s.kind << ":" << s.seed << ":" << s.t << ";";
+  return o.str();
+}
+
+mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, const View &vout, const ImgGeom &geo,
+                               const mrw_config &cfg, unsigned int *status, bool *used_status) {
+  const std::string key = image_program_key(p, geo, cfg, L.device, L.stream);
+  WhilePlan wp;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = while_plans().find(key);
+    if (it != while_plans().end()) wp = it->second;
+  }
+  if (!wp.exec) {
+    mrw_status s = build_while_plan(L, p, geo, cfg, &wp);
+    if (s != MRW_OK) {
+      destroy_while_plan(wp);
+      return s;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (while_plans().size() >= 16) {
+      cudaDeviceSynchronize();
+      for (auto &kv : while_plans()) destroy_while_plan(kv.second);
+      while_plans().clear();
+    }
+    while_plans()[key] = wp;
+  }
+  void *din, *dout;
+  int64_t pin, pout;
+  TRY(resolve(L, vin, true, false, &din, &pin));
+  TRY(resolve(L, vout, false, true, &dout, &pout));
+  const bool fused = cfg.fusion == MRW_FUSE_ALL;
+  const Program pre = sub_program(p, 0, p.while_begin);
+  const Program post = sub_program(p, p.while_end, (int)p.img.size());
+  if (pre.img.empty()) {
+    CU(cudaMemcpy2DAsync(wp.A, wp.pitch, din, pin, geo.W, geo.rows, cudaMemcpyDeviceToDevice, L.stream));
+  } else {
+    TRY(run_groups(L, group_stages(pre, fused, false), (const uint8_t *)din, pin, wp.A, wp.pitch, geo, cfg, p.wg,
+                   status, used_status, nullptr));
+  }
+  CU(cudaGraphLaunch(wp.exec, L.stream));
+  if (status) {
+    CU(cudaMemcpyAsync(status, wp.words + 1, sizeof(unsigned int), cudaMemcpyDeviceToDevice, L.stream));
+    *used_status = true;
+  }
+  if (post.img.empty()) {
+    CU(cudaMemcpy2DAsync(dout, pout, wp.A, wp.pitch, geo.W, geo.rows, cudaMemcpyDeviceToDevice, L.stream));
+  } else {
+    TRY(run_groups(L, group_stages(post, fused, false), wp.A, wp.pitch, (uint8_t *)dout, pout, geo, cfg, p.wg,
+                   status, used_status, nullptr));
+  }
+  return MRW_OK;
+}
+
 mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
                          unsigned int *status, bool *used_status) {
   View vin, vout, vred;
   TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
   const ImgGeom geo = geom_of(args[0], vin);
+  if (p.while_begin >= 0) return enqueue_image_while(L, p, vin, vout, geo, cfg, status, used_status);
   const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
   if (L.events && gs.size() == 1 && !gs[0].use_stencil && vin.b->memory == MRW_MEM_HOST &&
       vout.b->memory == MRW_MEM_HOST && geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20))
@@ -1059,39 +1367,7 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
     TRY(resolve(L, vred, false, true, &dred, &pred));
     red = (unsigned long long *)dred;  // overwritten by the last CTA of the reducing launch
   }
-  // intermediates between groups: at most two live at a time
-  bool any_stencil = false;
-  for (const Group &g : gs) any_stencil |= g.use_stencil;
-  if (any_stencil && status) CU(cudaMemsetAsync(status, 0, sizeof(unsigned int), L.stream));
-  const int64_t tpitch = round_up(geo.W, 16);
-  void *tmp[2] = {nullptr, nullptr};
-  int n_out_groups = 0;
-  for (const Group &g : gs) n_out_groups += !g.reduce_only;
-  if (n_out_groups > 1) TRY(L.alloc(&tmp[0], (size_t)(tpitch * geo.rows)));
-  if (n_out_groups > 2) TRY(L.alloc(&tmp[1], (size_t)(tpitch * geo.rows)));
-  const uint8_t *src = (const uint8_t *)din;
-  int64_t sp = pin;
-  int k = 0;
-  for (size_t gi = 0; gi < gs.size(); ++gi) {
-    const Group &g = gs[gi];
-    if (g.reduce_only) {
-      TRY(run_chain(L, g, src, sp, nullptr, 0, geo, cfg, p.wg, red));
-      continue;
-    }
-    ++k;
-    const bool last = k == n_out_groups;
-    uint8_t *dst = last ? (uint8_t *)dout : (uint8_t *)tmp[(k - 1) & 1];
-    const int64_t dp = last ? pout : tpitch;
-    if (g.use_stencil) {
-      TRY(run_stencil_single(L, g, src, sp, dst, dp, geo, cfg, status));
-      *used_status = true;
-    } else {
-      TRY(run_chain(L, g, src, sp, dst, dp, geo, cfg, p.wg, g.reduce != RED_NONE ? red : nullptr));
-    }
-    src = dst;
-    sp = dp;
-  }
-  return MRW_OK;
+  return run_groups(L, gs, (const uint8_t *)din, pin, (uint8_t *)dout, pout, geo, cfg, p.wg, status, used_status, red);
 }
 
 // ============================================================================================
@@ -1317,6 +1593,8 @@ mrw_status get_program(const mrw_node *root, Program *p) {
   if (!root) return fail(MRW_ERR_INVALID_ARG, "root is NULL");
   TRY(flatten(root, *p, 0, true, 1));
   if (p->fam == F_NONE) return fail(MRW_ERR_INVALID_ARG, "the tree has no stages");
+  if (p->while_begin >= 0 && p->reduce != RED_NONE)
+    return fail(MRW_ERR_UNSUPPORTED, "a WHILE_CHANGED loop inside a MapReduce");
   return MRW_OK;
 }
 
@@ -1484,7 +1762,8 @@ mrw_status mrw_mapreduce(mrw_node_t map_body, mrw_reduce_op op, mrw_node_t *out)
 mrw_status mrw_loop(mrw_node_t body, const mrw_loop_state *state, mrw_node_t *out) {
   if (!state) return fail(MRW_ERR_INVALID_ARG, "state is NULL");
   if (state->max_iters < 0 || state->max_iters > 100000000) return fail(MRW_ERR_INVALID_ARG, "max_iters out of range");
-  if (state->kind != MRW_LOOP_FOR) return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", state->kind);
+  if (state->kind != MRW_LOOP_FOR && state->kind != MRW_LOOP_WHILE_CHANGED)
+    return fail(MRW_ERR_UNSUPPORTED, "loop kind %d", state->kind);
   TRY(wrap(N_LOOP, body, out));
   (*out)->loop = *state;
   return MRW_OK;
@@ -1728,6 +2007,7 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
   TRY(get_program(root, &p));
   if (p.fam != F_IMAGE) return fail(MRW_ERR_UNSUPPORTED, "batched execution runs image trees");
   if (p.reduce != RED_NONE) return fail(MRW_ERR_UNSUPPORTED, "batched MapReduce");
+  if (p.while_begin >= 0) return fail(MRW_ERR_UNSUPPORTED, "batched WHILE_CHANGED loops");
   for (int64_t i = 0; i < n; ++i) {
     const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
     if (W < 1 || H < 1 || W > (1 << 20) || H > (1 << 20)) return fail(MRW_ERR_SHAPE, "instance %lld: bad size", (long long)i);
@@ -1824,7 +2104,12 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     const ImgGeom geo = geom_of(args[0], vin);
     const std::vector<Group> gs = group_stages(p, c.fusion == MRW_FUSE_ALL, false);
     o << "{\"family\":\"image\",\"W\":" << geo.W << ",\"H\":" << geo.H << ",\"D\":" << geo.D
-      << ",\"reduce\":" << p.reduce << ",\"groups\":[";
+      << ",\"reduce\":" << p.reduce;
+    if (p.while_begin >= 0)
+      o << ",\"while_changed\":{\"first_stage\":" << p.while_begin << ",\"end_stage\":" << p.while_end
+        << ",\"max_iters\":" << p.while_max << ",\"body_kernels\":"
+        << group_stages(sub_program(p, p.while_begin, p.while_end), c.fusion == MRW_FUSE_ALL, false).size() << "}";
+    o << ",\"groups\":[";
     for (size_t i = 0; i < gs.size(); ++i) {
       const Group &g = gs[i];
       o << (i ? "," : "") << "{";

@@ -146,6 +146,14 @@ cudaError_t build_nbody_loop_graph(const NBodyParams &p, LoopCtrl *ctrl, int64_t
 cudaError_t launch_saxpy(const float *x, float *y, int64_t n, float alpha, int grid, int block, cudaStream_t s);
 cudaError_t launch_fill_u32(unsigned int *p, unsigned int v, int64_t n, cudaStream_t s);
 
+// WHILE_CHANGED loops: a := b where they differ and *changed := 1 if any byte differed; the
+// control kernel counts the run and sets the WHILE node's condition (changed && iter < max).
+cudaError_t launch_compare_copy(const uint8_t *b, uint8_t *a, int64_t rows, int32_t W, int64_t pitch,
+                                unsigned int *changed, int sms, cudaStream_t s);
+cudaError_t launch_while_control(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, cudaStream_t s);
+// words[0] (changed flag) and words[1] (body status word) are zeroed with the counter.
+cudaError_t launch_while_init(LoopCtrl *ctrl, unsigned int *words, unsigned long long max_iters, cudaStream_t s);
+
 // ------------------------------------------------------------------------------------------
 // Cost-model MLP (bf16 weights, fp32 accumulation)
 // ------------------------------------------------------------------------------------------

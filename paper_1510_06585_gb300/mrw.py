@@ -21,7 +21,7 @@ MRW_PARTITION, MRW_COPY = 0, 1
 (MRW_ST_NOISE_HASH, MRW_ST_SOLARISE, MRW_ST_MIRROR_H, MRW_ST_BOXBLUR5, MRW_ST_THRESHOLD3,
  MRW_ST_NBODY_ACCEL, MRW_ST_NBODY_KDK, MRW_ST_SAXPY) = range(8)
 MRW_RED_ADD, MRW_RED_SUB, MRW_RED_MUL, MRW_RED_DIV = range(4)
-MRW_LOOP_FOR = 0
+MRW_LOOP_FOR, MRW_LOOP_WHILE_CHANGED = 0, 1
 MRW_FUSE_ALL, MRW_FUSE_NONE = 0, 1
 MRW_TUNE_EXHAUSTIVE, MRW_TUNE_PRUNED, MRW_TUNE_MODEL = 0, 1, 2
 MRW_NFEATURES = 16
@@ -273,9 +273,9 @@ def mapreduce(body: Node, op: int = MRW_RED_ADD) -> Node:
     return Node(out)
 
 
-def loop(body: Node, iters: int) -> Node:
+def loop(body: Node, iters: int, kind: int = MRW_LOOP_FOR) -> Node:
     st = mrw_loop_state()
-    st.max_iters, st.kind, st.global_sync = iters, MRW_LOOP_FOR, 1
+    st.max_iters, st.kind, st.global_sync = iters, kind, 1
     out = ctypes.c_void_p()
     check(load().mrw_loop(body.h, ctypes.byref(st), ctypes.byref(out)), "mrw_loop")
     return Node(out)

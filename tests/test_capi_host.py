@@ -199,3 +199,20 @@ def test_candidates_are_sixteen_valid_configs(lib):
     assert len(cfgs) == 16
     assert cfgs[0].fusion == mrw.MRW_FUSE_ALL and cfgs[8].fusion == mrw.MRW_FUSE_NONE
     assert len({c.as_tuple() for c in cfgs}) == 16
+
+
+def test_while_changed_loops_are_planned_and_validated(lib):
+    blur = mrw.stage("blur5")
+    w = mrw.loop(blur, 500, mrw.MRW_LOOP_WHILE_CHANGED)
+    d = mrw.plan_describe(mrw.pipeline(mrw.stage("noise", seed=1), w, mrw.stage("solarise")), _image_args(40, 50))
+    assert d["while_changed"] == {"first_stage": 1, "end_stage": 2, "max_iters": 500, "body_kernels": 1}
+    with pytest.raises(mrw.MrwError) as e:   # one convergence loop per tree
+        mrw.plan_describe(mrw.pipeline(w, mrw.loop(blur, 3, mrw.MRW_LOOP_WHILE_CHANGED)), _image_args())
+    assert e.value.status == mrw.MRW_ERR_UNSUPPORTED
+    with pytest.raises(mrw.MrwError) as e:   # not inside a MapReduce
+        mrw.plan_describe(mrw.mapreduce(mrw.pipeline(w, mrw.stage("threshold3"))), _image_args(reduce=True))
+    assert e.value.status == mrw.MRW_ERR_UNSUPPORTED
+    with pytest.raises(mrw.MrwError) as e:   # image trees only
+        mrw.plan_describe(mrw.loop(mrw.stage("nbody_kdk", eps=1e-3, dt=1e-3), 5, mrw.MRW_LOOP_WHILE_CHANGED),
+                          _nbody_args(16))
+    assert e.value.status == mrw.MRW_ERR_UNSUPPORTED

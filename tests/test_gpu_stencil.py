@@ -128,3 +128,35 @@ def test_batched_rejects_bad_descriptors():
     with pytest.raises(M.MrwError) as e:
         M.execute_batched(tree, x, y, bad)
     assert e.value.status == M.MRW_ERR_SHAPE
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (64, 64), (100, 137), (3, 40)])
+def test_blur_until_fixed_point_is_decided_on_the_device(shape):
+    img = inputs.filter_image(*shape, seed=shape[0])
+    tree = M.loop(M.stage("blur5"), 1000, M.MRW_LOOP_WHILE_CHANGED)
+    want, _ = S.evaluate_image(("loop_while", ("stage", "blur5", {}), 1000), img)
+    for cfg in (None, M.config(tile_rows=16, tile_cols=64)):
+        got, _ = run_image(tree, img, cfg)
+        assert np.array_equal(got, want), shape
+    assert np.array_equal(O.blur5(want), want)
+
+
+def test_while_loop_inside_a_pipeline_and_capped_bodies():
+    img = inputs.filter_image(70, 90, seed=4)
+    body = M.pipeline(M.stage("mirror"), M.stage("blur5"), M.stage("noise", seed=3), M.stage("blur5"))
+    for cap in (1, 7, 400):
+        tree = M.pipeline(M.stage("noise", seed=9), M.loop(body, cap, M.MRW_LOOP_WHILE_CHANGED),
+                          M.stage("solarise"))
+        otree = ("pipeline", [("stage", "noise", {"seed": 9}),
+                              ("loop_while", ("pipeline", [("stage", "mirror", {}), ("stage", "blur5", {}),
+                                                          ("stage", "noise", {"seed": 3}), ("stage", "blur5", {})]),
+                               cap),
+                              ("stage", "solarise", {})])
+        want, _ = S.evaluate_image(otree, img)
+        for cfg in (M.config(), M.config(fusion=M.MRW_FUSE_NONE)):
+            for _ in range(2):  # the second run reuses the cached loop graph
+                got, _ = run_image(tree, img, cfg)
+                assert np.array_equal(got, want), (cap, cfg.as_tuple())
+    # an idempotent pointwise body stops after its second run
+    got, _ = run_image(M.loop(M.stage("solarise"), 50, M.MRW_LOOP_WHILE_CHANGED), img)
+    assert np.array_equal(got, O.solarise(img))

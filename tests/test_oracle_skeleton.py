@@ -67,3 +67,22 @@ def test_nbody_tree_is_accel_then_loop():
     assert trace == ["nbody_accel"] + ["nbody_kdk"] * 5
     for g, w in zip(got, want):
         assert np.array_equal(np.asarray(g)[:, :3], np.asarray(w)[:, :3])
+
+
+def test_loop_while_changed_stops_at_the_fixed_point():
+    img = inputs.filter_image(16, 16, seed=16)
+    trace = []
+    out, _ = S.evaluate_image(("loop_while", st("blur5"), 1000), img, trace)
+    assert np.array_equal(I.blur5(out), out)          # a fixed point of the body
+    n = len(trace)                                    # run n made no change, run n - 1 did
+    prev = img
+    for _ in range(n - 2):
+        prev = I.blur5(prev)
+    assert not np.array_equal(I.blur5(prev), prev)
+    assert np.array_equal(I.blur5(I.blur5(prev)), I.blur5(prev))
+    capped, _ = S.evaluate_image(("loop_while", st("blur5"), 3), img)
+    assert np.array_equal(capped, I.blur5(I.blur5(I.blur5(img))))
+    # an idempotent body stops after its second run
+    t2 = []
+    S.evaluate_image(("loop_while", st("solarise"), 50), img, t2)
+    assert len(t2) == 2
