@@ -308,7 +308,7 @@ def run_mrw(args):
                      "unit": "GB/s", "frac": round(SEG_BYTES / fused_s / 1e9 / peaks["hbm_gbs"], 4),
                      "traffic": recorded_traffic("k_chain.cu", "segmentation_512cubed_chain"),
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
-                     "note": "achieved = algorithmic bytes / CUDA-event time of the step (chain kernel + 24-byte memset)"},
+                     "note": "achieved = algorithmic bytes / CUDA-event time of the step (one chain-kernel launch per step; the MapReduce finishes inside it)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
                 "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e},
         "gpu_launches": K,

@@ -214,6 +214,12 @@ void mrw_node_release(mrw_node_t n);
  * mrw_future_release). `cfg` may be NULL (tuned or default configuration). */
 mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
                        void *stream, mrw_future_t *out);
+/* As mrw_execute, and the future also records the call's device time for
+ * mrw_future_elapsed_ms. Timing costs a pair of timing-enabled events on the stream around the
+ * call (several microseconds per call on a busy stream), so mrw_execute records only an
+ * ordering event. */
+mrw_status mrw_execute_timed(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
+                             void *stream, mrw_future_t *out);
 
 /* Batched execution (many independent instances of one image tree in one persistent launch):
  * instance i reads in_arena + desc[5i] and writes out_arena + desc[5i] with
@@ -259,7 +265,8 @@ mrw_status mrw_future_wait(mrw_future_t f, int64_t timeout_ms);
 /* Non-blocking: MRW_OK when done, MRW_ERR_NOT_READY while running, errors as mrw_future_wait. */
 mrw_status mrw_future_query(mrw_future_t f);
 /* Device time between the first and the last enqueued operation of the call, in ms (after
- * completion). */
+ * completion). Only futures of mrw_execute_timed carry it; any other future gives
+ * MRW_ERR_INVALID_ARG. */
 mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms);
 void mrw_future_release(mrw_future_t f);
 

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
   }
 
   if (s_fail && tid == 0) {
-    atomicOr(a.status, 1u);
+    *(volatile unsigned int *)a.status = 1u;  // may be mapped host memory
     // let the copies this CTA issued land before it leaves (bounded as well)
     if (s_tile[cur ^ 1] < a.total_tiles) (void)mbar_wait_bounded(&bar[cur ^ 1], (phases >> (cur ^ 1)) & 1u);
     (void)mbar_wait_bounded(&bar[cur], (phases >> cur) & 1u);

@@ -102,12 +102,16 @@ class StatusPool {
   mrw_status take(StatusSlot *out) {
     std::lock_guard<std::mutex> lk(mu_);
     if (free_.empty()) {
+      // mapped pinned words: kernels write a failure straight into host memory, so a call needs
+      // neither a reset nor a copy of its status word
       const int n = 1024;
       unsigned int *d = nullptr, *h = nullptr;
-      CU(cudaMalloc(&d, n * sizeof(unsigned int)));
-      if (cudaHostAlloc(&h, n * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
-        cudaFree(d);
+      if (cudaHostAlloc(&h, n * sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess)
         return fail(MRW_ERR_OOM, "pinned status words");
+      memset(h, 0, n * sizeof(unsigned int));
+      if (cudaHostGetDevicePointer((void **)&d, h, 0) != cudaSuccess) {
+        cudaFreeHost(h);
+        return fail(MRW_ERR_CUDA, "cudaHostGetDevicePointer(status words)");
       }
       const int b = (int)blocks_.size();
       blocks_.push_back({d, h});
@@ -124,6 +128,7 @@ class StatusPool {
   }
   void give(const StatusSlot &s) {
     if (s.idx < 0) return;
+    *(volatile unsigned int *)s.host = 0u;
     std::lock_guard<std::mutex> lk(mu_);
     free_.push_back({s.block, s.idx});
   }
@@ -268,7 +273,8 @@ struct mrw_node {
 };
 
 struct mrw_future {
-  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;  // start is set (and done times) only when timed
+  bool timed = false;
   int device = 0;
   StatusSlot slot;
   bool has_status = false;
@@ -790,6 +796,12 @@ ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, 
   return s;
 }
 
+// Test hook of the failure-detection tests: make a bounded wait give up early.
+uint32_t test_wait_polls() {
+  const char *e = getenv("MRW_TEST_WAIT_POLLS");
+  return e ? (uint32_t)strtoul(e, nullptr, 10) : 0u;
+}
+
 mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op,
                      const ImgGeom &geo, const mrw_config &cfg, int wg, unsigned long long *red) {
   ChainArgs a{};
@@ -834,11 +846,6 @@ StencilShape stencil_shape(const mrw_config &cfg, int halo) {
   s.cps = std::min(8, cfg.ctas_per_sm ? cfg.ctas_per_sm : 4);
   s.smem = stencil_smem_bytes(s.tile_h, s.tile_w, halo);
   return s;
-}
-
-uint32_t test_wait_polls() {
-  const char *e = getenv("MRW_TEST_WAIT_POLLS");
-  return e ? (uint32_t)strtoul(e, nullptr, 10) : 0u;
 }
 
 void fill_stencil_ops(const Group &g, StencilArgs &a) {
@@ -993,9 +1000,6 @@ ImgGeom geom_of(const mrw_buffer &b, const View &v) {
 mrw_status run_groups(Launch &L, const std::vector<Group> &gs, const uint8_t *src, int64_t sp, uint8_t *dst,
                       int64_t dp_final, const ImgGeom &geo, const mrw_config &cfg, int wg, unsigned int *status,
                       bool *used_status, unsigned long long *red) {
-  bool any_stencil = false;
-  for (const Group &g : gs) any_stencil |= g.use_stencil;
-  if (any_stencil && status) CU(cudaMemsetAsync(status, 0, sizeof(unsigned int), L.stream));
   const int64_t tpitch = round_up(geo.W, 16);
   void *tmp[2] = {nullptr, nullptr};
   int n_out_groups = 0;
@@ -1334,7 +1338,7 @@ mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, con
   }
   CU(cudaGraphLaunch(wp.exec, L.stream));
   if (status) {
-    CU(cudaMemcpyAsync(status, wp.words + 1, sizeof(unsigned int), cudaMemcpyDeviceToDevice, L.stream));
+    CU(cudaMemcpyAsync(status, wp.words + 1, sizeof(unsigned int), cudaMemcpyDefault, L.stream));
     *used_status = true;
   }
   if (post.img.empty()) {
@@ -1666,10 +1670,21 @@ mrw_status begin_launch(Launch &L, void *stream) {
   return MRW_OK;
 }
 
+// The future's completion event: an ordering-only event, or a timing pair when asked for.
+mrw_status take_future_events(mrw_future *f, bool timed) {
+  f->timed = timed;
+  if (timed) return event_pool().take(&f->start, &f->done);
+  return get_sync_event(&f->done);
+}
+
 void free_future(mrw_future *f) {
   if (!f) return;
+  if (f->timed) {
+    event_pool().give(f->start, f->done);
+  } else if (f->done) {
+    f->sync_events.push_back(f->done);
+  }
   put_sync_events(f->sync_events);
-  event_pool().give(f->start, f->done);
   status_pool().give(f->slot);
   delete f;
 }
@@ -1775,8 +1790,11 @@ void mrw_node_retain(mrw_node_t n) {
 
 void mrw_node_release(mrw_node_t n) { release_node(n); }
 
-mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg, void *stream,
-                       mrw_future_t *out) {
+}  // extern "C"
+
+namespace {
+mrw_status execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg, void *stream,
+                   mrw_future_t *out, bool timed) {
   if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
@@ -1791,17 +1809,16 @@ mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, c
   if (!f) return fail(MRW_ERR_OOM, "future");
   f->device = L.device;
   mrw_status s = status_pool().take(&f->slot);
-  if (s == MRW_OK) s = event_pool().take(&f->start, &f->done);
+  if (s == MRW_OK) s = take_future_events(f, timed);
   if (s != MRW_OK) {
     free_future(f);
     return s;
   }
-  cudaEventRecord(f->start, L.stream);
+  if (timed) cudaEventRecord(f->start, L.stream);
   bool used = false;
   L.events = &f->sync_events;
   s = enqueue(L, p, args, nargs, c, f->slot.dev, &used);
-  if (used) cudaMemcpyAsync(f->slot.host, f->slot.dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, L.stream);
-  f->has_status = used;
+  f->has_status = used;  // kernels write failures into the mapped host word itself
   L.free_all();
   cudaEventRecord(f->done, L.stream);
   if (s != MRW_OK) {
@@ -1814,6 +1831,19 @@ mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, c
   }
   *out = f;
   return MRW_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg, void *stream,
+                       mrw_future_t *out) {
+  return execute(root, args, nargs, cfg, stream, out, false);
+}
+
+mrw_status mrw_execute_timed(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
+                             void *stream, mrw_future_t *out) {
+  return execute(root, args, nargs, cfg, stream, out, true);
 }
 
 mrw_status mrw_future_query(mrw_future_t f) {
@@ -1845,6 +1875,7 @@ mrw_status mrw_future_wait(mrw_future_t f, int64_t timeout_ms) {
 
 mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms) {
   if (!f || !ms) return fail(MRW_ERR_INVALID_ARG, "NULL argument");
+  if (!f->timed) return fail(MRW_ERR_INVALID_ARG, "the future records no time: run with mrw_execute_timed");
   const cudaError_t e = cudaEventElapsedTime(ms, f->start, f->done);
   if (e == cudaErrorNotReady) return MRW_ERR_NOT_READY;
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
@@ -2050,12 +2081,11 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
   if (!f) return fail(MRW_ERR_OOM, "future");
   f->device = L.device;
   mrw_status s = status_pool().take(&f->slot);
-  if (s == MRW_OK) s = event_pool().take(&f->start, &f->done);
+  if (s == MRW_OK) s = take_future_events(f, false);
   if (s != MRW_OK) {
     free_future(f);
     return s;
   }
-  cudaEventRecord(f->start, L.stream);
   cudaError_t e = cudaGraphLaunch(plan.exec, L.stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(f->slot.host, plan.counters + plan.ngroups, sizeof(unsigned int), cudaMemcpyDeviceToHost,

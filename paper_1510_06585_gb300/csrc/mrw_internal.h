@@ -82,7 +82,7 @@ struct StencilArgs {
   const uint8_t *in_base;
   uint8_t *out_base;
   unsigned int *queue;              // tile counter, zeroed before the launch
-  unsigned int *status;             // device status word (bounded waits)
+  unsigned int *status;             // status word (bounded waits); may be mapped host memory
   int64_t total_tiles;
   int32_t ninst;
   int32_t halo;                     // 2 with a blur, 0 for a pointwise-only group

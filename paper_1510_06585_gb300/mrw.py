@@ -73,6 +73,8 @@ _SIGS = {
     "mrw_node_release": (None, [_P]),
     "mrw_execute": (ctypes.c_int, [_P, ctypes.POINTER(mrw_buffer), ctypes.c_int32, ctypes.POINTER(mrw_config), _P,
                                    ctypes.POINTER(_P)]),
+    "mrw_execute_timed": (ctypes.c_int, [_P, ctypes.POINTER(mrw_buffer), ctypes.c_int32, ctypes.POINTER(mrw_config),
+                                         _P, ctypes.POINTER(_P)]),
     "mrw_execute_batched": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                            ctypes.POINTER(mrw_config), _P, ctypes.POINTER(_P)]),
     "mrw_execute_batched_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
@@ -305,13 +307,15 @@ class Future:
             self.h = None
 
 
-def execute(root: Node, args, cfg: mrw_config | None = None, stream=None) -> Future:
-    """Enqueue root on args (tensors / arrays / mrw_buffer); returns a Future."""
+def execute(root: Node, args, cfg: mrw_config | None = None, stream=None, timed: bool = False) -> Future:
+    """Enqueue root on args (tensors / arrays / mrw_buffer); returns a Future. With timed=True
+    the future also records device time (Future.elapsed_ms) through mrw_execute_timed."""
     arr = buffers(*args)
     out = ctypes.c_void_p()
     st = stream_handle(stream) if stream is not None or _cuda_available() else None
-    check(load().mrw_execute(root.h, arr, len(args), ctypes.byref(cfg) if cfg is not None else None, st,
-                             ctypes.byref(out)), "mrw_execute")
+    fn = load().mrw_execute_timed if timed else load().mrw_execute
+    check(fn(root.h, arr, len(args), ctypes.byref(cfg) if cfg is not None else None, st, ctypes.byref(out)),
+          "mrw_execute_timed" if timed else "mrw_execute")
     return Future(out)
 
 

@@ -144,10 +144,19 @@ def test_in_place_pointwise_chain():
 
 def test_future_elapsed_and_query():
     img = inputs.filter_image(512, 512)
-    f = M.execute(build_image_tree(FILTER, {0: 2}), [to_device(img), empty_like_device(img)])
+    x, y = to_device(img), empty_like_device(img)
+    tree = build_image_tree(FILTER, {0: 2})
+    f = M.execute(tree, [x, y], timed=True)
     f.wait(60000)
     assert f.elapsed_ms() > 0
     assert M.load().mrw_future_query(f.h) == M.MRW_OK
+    assert np.array_equal(y.cpu().numpy(), O.filter_pipeline(img, 2))
+    # an untimed future (the default) has no device time to report
+    g = M.execute(tree, [x, y])
+    g.wait(60000)
+    with pytest.raises(M.MrwError) as e:
+        g.elapsed_ms()
+    assert e.value.status == M.MRW_ERR_INVALID_ARG
 
 
 def test_large_host_buffers_take_the_overlapped_chunked_path():
