@@ -117,31 +117,36 @@ __device__ __forceinline__ void noise16(uint32_t (&w)[4], const uint32_t (&ch)[1
   }
 }
 
-// Applies the chain; for a trailing threshold also returns the per-byte ">= t0" / ">= t1" flags
-// (0x01 per byte) so the class counts need no further compares.
-template <int NN>
-__device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (&w)[4],
-                                            const uint32_t (&ch)[NN > 0 ? NN : 1][16], uint32_t ypre,
-                                            uint32_t (&g0)[4], uint32_t (&g1)[4]) {
+// Applies the chain to U segments: each op is decoded once and applied to all of them, which also
+// gives the scheduler U independent dependency chains. Chains with noise stages call it one segment
+// at a time (U = 1): their 16 hashes a segment already give the scheduler enough independent work,
+// and U segments in flight would exhaust the registers.
+template <int NN, int U>
+__device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4],
+                                            const uint32_t (&ch)[NN > 0 ? NN : 1][16], const uint32_t *ypre) {
   int kn = 0;
   for (int i = 0; i < a.nops; ++i) {
     const int kind = a.ops[i].kind;
     if (kind == OP_SOLARISE) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = solarise4(w[j]);
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[u][j] = solarise4(w[u][j]);
     } else if (kind == OP_THRESH) {
       const Thresh t = make_thresh(a.ops[i].t);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        g0[j] = ge4(w[j], t.t0, t.t0lo) >> 7;
-        g1[j] = ge4(w[j], t.t1, t.t1lo) >> 7;
-        w[j] = g0[j] + g1[j];
-      }
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          w[u][j] = (ge4(w[u][j], t.t0, t.t0lo) >> 7) + (ge4(w[u][j], t.t1, t.t1lo) >> 7);
     } else if (kind == OP_NOISE) {
       if constexpr (NN >= 1) {
-        if (kn == 0) noise16(w, ch[0], ypre);
-        if constexpr (NN >= 2) {
-          if (kn == 1) noise16(w, ch[1], ypre);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (kn == 0) noise16(w[u], ch[0], ypre[u]);
+          if constexpr (NN >= 2) {
+            if (kn == 1) noise16(w[u], ch[1], ypre[u]);
+          }
         }
       }
       ++kn;
@@ -154,8 +159,10 @@ __device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01
 
 template <int NN, bool MIR, int U>
 __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ ChainArgs a) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nthreads = a.rows_parallel * a.col_vecs;
+  // grid * block <= 2^30 threads (kMaxChainGrid CTAs of at most 256): 32-bit thread indices
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t cv = (uint32_t)a.col_vecs;
+  const uint32_t nthreads = (uint32_t)a.rows_parallel * cv;
   // class counts: ge0 = #(label >= 1), ge1 = #(label == 2), n = pixels seen
   uint32_t cnt_ge0 = 0, cnt_ge1 = 0, cnt_n = 0;
   unsigned long long vsum = 0;
@@ -164,9 +171,15 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (gid >= nthreads) asm volatile("griddepcontrol.wait;" ::: "memory");
   if (gid < nthreads) {
-    const int col = (int)(gid % a.col_vecs);
-    const int64_t r0 = gid / a.col_vecs;
-    const int xo = col * 16;
+    uint32_t col, r0;
+    if ((cv & (cv - 1)) == 0) {  // power-of-two segment count (W a multiple of 16 * 2^k)
+      col = gid & (cv - 1);
+      r0 = gid >> (__ffs(cv) - 1);
+    } else {
+      r0 = gid / cv;
+      col = gid - r0 * cv;
+    }
+    const int xo = (int)col * 16;
     const int W = a.W;
     const int nv = min(16, W - xo);
     const bool full = nv == 16;
@@ -206,75 +219,77 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
       const int nb = min(max(nv - 4 * j, 0), 4);
       vmask[j] = nb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
     }
-    const bool last_thresh = a.nops > 0 && a.ops[a.nops - 1].kind == OP_THRESH;
-    uint32_t lane0 = 0, lane1 = 0;  // byte-lane counters, folded every 63 segments
+    // byte-lane counters: lane0 sums the label bytes (n1 + 2 n2), lane1 sums their bit 1 (2 n2);
+    // each lane grows by at most 8 a segment
+    uint32_t lane0 = 0, lane1 = 0;
     int since_fold = 0;
+    // persistent order: rows r0 + (k U + u) step; blocked order: rows (r0 + k step) U + u
     const int64_t step = a.rows_parallel;
-    for (int64_t y0 = r0; y0 < a.rows; y0 += U * step) {
-      uint4 v[U];
+    const int64_t ustep = a.blocked ? 1 : step;
+    for (int64_t y0 = a.blocked ? (int64_t)r0 * U : (int64_t)r0; y0 < a.rows; y0 += U * step) {
+      uint32_t w[U][4], ypre[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t y = y0 + u * step;
+        const int64_t y = y0 + u * ustep;
+        uint4 v = make_uint4(0, 0, 0, 0);
         if (y < a.rows) {
           const uint8_t *row = a.in + y * a.in_pitch;
-          v[u] = MIR ? load_mirrored(row, xo, W, q0, sel) : ld16(row + xo);
+          v = MIR ? load_mirrored(row, xo, W, q0, sel) : ld16(row + xo);
         }
+        w[u][0] = v.x;
+        w[u][1] = v.y;
+        w[u][2] = v.z;
+        w[u][3] = v.w;
+        const uint32_t y32 = (uint32_t)(y + a.row0);
+        ypre[u] = y32 ^ (y32 >> 16);
+      }
+      if constexpr (NN == 0) {
+        apply_chain<0, U>(a, w, ch, ypre);
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) apply_chain<NN, 1>(a, &w[u], ch, &ypre[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t y = y0 + u * step;
-        if (y < a.rows) {
-          uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-          uint32_t g0[4] = {0, 0, 0, 0}, g1[4] = {0, 0, 0, 0};
-          const uint32_t y32 = (uint32_t)(y + a.row0);
-          apply_chain<NN>(a, w, ch, y32 ^ (y32 >> 16), g0, g1);
-          if (a.reduce == RED_COUNT3 && !last_thresh) {
-            // counting labels written by an earlier kernel (kernel-per-stage MapReduce)
+        const int64_t y = y0 + u * ustep;
+        if (y >= a.rows) break;
+        if (a.reduce == RED_COUNT3) {
+          // label bytes 0, 1, 2 (a threshold stage's output): with n1, n2 the counts of labels 1
+          // and 2, the byte sum is n1 + 2 n2 and the sum of bit 1 is 2 n2
+          const uint32_t m0 = w[u][0] & vmask[0], m1 = w[u][1] & vmask[1];
+          const uint32_t m2 = w[u][2] & vmask[2], m3 = w[u][3] & vmask[3];
+          lane0 += (m0 + m1) + (m2 + m3);
+          lane1 += ((m0 & 0x02020202u) + (m1 & 0x02020202u)) + ((m2 & 0x02020202u) + (m3 & 0x02020202u));
+          cnt_n += nv;
+        } else if (a.reduce == RED_SUM) {
+          uint32_t s4 = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              g0[j] = ge4(w[j], 0x01010101u, 0x01010101u) >> 7;
-              g1[j] = ge4(w[j], 0x02020202u, 0x02020202u) >> 7;
-            }
-          }
-          if (a.reduce == RED_COUNT3) {
-            if (full) {
-              lane0 += (g0[0] + g0[1]) + (g0[2] + g0[3]);
-              lane1 += (g1[0] + g1[1]) + (g1[2] + g1[3]);
-            } else {
+          for (int j = 0; j < 4; ++j) s4 = __dp4a(w[u][j] & vmask[j], 0x01010101u, s4);
+          vsum += s4;
+        }
+        if (a.out) {
+          uint8_t *orow = a.out + y * a.out_pitch + xo;
+          if (full) {
+            __stcs(reinterpret_cast<uint4 *>(orow), make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]));
+          } else {
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                lane0 += g0[j] & vmask[j];
-                lane1 += g1[j] & vmask[j];
-              }
-            }
-            cnt_n += nv;
-            if (++since_fold == 63) {
-              cnt_ge0 += byte_sum(lane0);
-              cnt_ge1 += byte_sum(lane1);
-              lane0 = lane1 = 0;
-              since_fold = 0;
-            }
-          } else if (a.reduce == RED_SUM) {
-            uint32_t s4 = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) s4 = __dp4a(w[j] & vmask[j], 0x01010101u, s4);
-            vsum += s4;
-          }
-          if (a.out) {
-            uint8_t *orow = a.out + y * a.out_pitch + xo;
-            if (full) {
-              __stcs(reinterpret_cast<uint4 *>(orow), make_uint4(w[0], w[1], w[2], w[3]));
-            } else {
-#pragma unroll
-              for (int k = 0; k < 16; ++k)
-                if (k < nv) orow[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
-            }
+            for (int k = 0; k < 16; ++k)
+              if (k < nv) orow[k] = (uint8_t)(w[u][k >> 2] >> (8 * (k & 3)));
           }
         }
+      }
+      if (a.reduce == RED_COUNT3 && (since_fold += U) > 31 - U) {  // fold before a lane reaches 256
+        cnt_ge0 += byte_sum(lane0);
+        cnt_ge1 += byte_sum(lane1);
+        lane0 = lane1 = 0;
+        since_fold = 0;
       }
     }
     cnt_ge0 += byte_sum(lane0);
     cnt_ge1 += byte_sum(lane1);
+    // cnt_ge0 = n1 + 2 n2 and cnt_ge1 = 2 n2 here: make them #(label >= 1) and #(label == 2)
+    cnt_ge1 >>= 1;
+    cnt_ge0 -= cnt_ge1;
   }
 
   if (a.reduce == RED_NONE) return;
@@ -311,23 +326,42 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Chai
       t[1] += red_smem[i][1];
       t[2] += red_smem[i][2];
     }
-    // with a workspace: add into its accumulator (left at zero by the previous launch), and let
-    // the last CTA to arrive move the totals into `red`; without: add into a zeroed `red`
-    unsigned long long *dst = a.partials ? a.partials : a.red;
+    // with a workspace: add into accumulator set blockIdx % kChainSlots (left at zero by the
+    // previous launch), and let the last CTA to arrive sum the sets into `red`; without: add into
+    // a zeroed `red`
+    unsigned long long *dst = a.partials ? a.partials + 3 * (blockIdx.x % kChainSlots) : a.red;
     for (int k = 0; k < nout; ++k)
       if (t[k]) atomicAdd(dst + k, t[k]);
     is_last = false;
     if (a.partials) {
-      __threadfence();
+      // release: this CTA's adds are visible before its ticket; acquire on the last CTA's side.
+      // acq_rel is enough for this pattern; the sequentially consistent __threadfence() would also
+      // wait for the thread's streaming stores of the image.
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
       is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
   }
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
-  __threadfence();
+  if (!is_last) return;  // uniform over the CTA
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  unsigned long long v[3] = {0, 0, 0};
+  for (int sl = threadIdx.x; sl < kChainSlots; sl += blockDim.x)
+    for (int k = 0; k < nout; ++k) {
+      v[k] += __ldcg(a.partials + 3 * sl + k);
+      a.partials[3 * sl + k] = 0ull;  // clean for the next launch on this workspace
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    for (int k = 0; k < 3; ++k) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) red_smem[warp][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int nw = (blockDim.x + 31) >> 5;
   for (int k = 0; k < nout; ++k) {
-    a.red[k] = __ldcg(a.partials + k);
-    a.partials[k] = 0ull;  // clean for the next launch on this workspace
+    unsigned long long tot = 0;
+    for (int i = 0; i < nw; ++i) tot += red_smem[i][k];
+    a.red[k] = tot;
   }
   *a.ticket = 0u;
 }

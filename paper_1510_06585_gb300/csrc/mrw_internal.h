@@ -37,26 +37,30 @@ struct ChainArgs {
   uint8_t *out;            // nullptr: reduce only
   int64_t in_pitch, out_pitch;
   int64_t rows;            // total rows (D * H)
-  int64_t rows_parallel;   // rows a wave of threads covers; a thread steps rows by this
+  int64_t rows_parallel;   // row positions the threads cover at once (rows / unroll when blocked)
   int32_t W;
   int32_t col_vecs;        // ceil(W / 16)
   int32_t nops;
   int32_t mirror;          // parity of mirror ops in the chain: source column = W-1-x
   int32_t reduce;          // RedKind
-  int32_t pad_;
+  // row order of a thread: 0 = persistent (rows r0, r0 + rows_parallel, ...; one wave of CTAs),
+  // 1 = blocked (unroll consecutive rows r0 * unroll + u; many short CTAs)
+  int32_t blocked;
   unsigned long long *red; // RED_COUNT3: [3] counts; RED_SUM: [1]
-  // MapReduce finish: with `partials` set (a per-stream workspace whose 3 accumulators and ticket
-  // are zero between launches), CTAs add into the accumulators and the last CTA to arrive (ticket)
-  // moves them into `red` and zeroes them again; with `partials` null, CTAs add into a zeroed `red`
-  // (used when several launches accumulate into one result).
+  // MapReduce finish: with `partials` set (a per-stream workspace of kChainSlots sets of 3
+  // accumulators and a ticket, all zero between launches), CTA b adds into set b % kChainSlots and
+  // the last CTA to arrive (ticket) sums the sets into `red` and zeroes them again; spreading the
+  // adds over the sets keeps thousands of CTAs from queueing on one address. With `partials` null,
+  // CTAs add into a zeroed `red` (used when several launches accumulate into one result).
   unsigned long long *partials;
   unsigned int *ticket;
   int64_t row0;            // global row of the first row (the Offset trait, for the noise hash)
   ChainOp ops[kMaxChainOps];
 };
 
-// Largest grid a chain launch may use with an in-kernel MapReduce finish (workspace size).
-constexpr int kMaxChainGrid = 4096;
+// Accumulator sets of the in-kernel MapReduce finish, and the largest grid of a chain launch.
+constexpr int kChainSlots = 64;
+constexpr int kMaxChainGrid = 1 << 22;
 
 // Resident CTAs per SM of a chain-kernel variant (occupancy query, cached).
 int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block);
