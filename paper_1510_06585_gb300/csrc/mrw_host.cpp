@@ -782,19 +782,27 @@ struct ChainShape {
 // Launch shape of a chain group; each thread keeps one 16-byte column segment. Chains with noise
 // stages run one wave of resident CTAs (the occupancy of the kernel variant caps ctas_per_sm) so a
 // thread's per-column hash halves serve many rows. Chains without them are pure streaming: every
-// thread takes `unroll` consecutive rows once, in many short CTAs that the hardware schedules as
-// SMs free up (measured on GB300: a 128 MiB copy in this order runs about 5 % faster than the
-// one-wave order).
+// thread takes `unroll` consecutive rows at a time in short CTAs that the hardware schedules as SMs
+// free up (measured on GB300: a 128 MiB copy in this order runs about 5 % faster than the one-wave
+// order). There the grid is capped at `waves` x sms x ctas_per_sm CTAs: 8 waves for a map, 2 for a
+// MapReduce group, whose CTAs each pay a finish (block reduction, adds, ticket).
 ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, int wg, int n_noise,
-                       bool mirror = false, bool query_occupancy = false) {
+                       bool mirror = false, bool query_occupancy = false, bool reduce = false) {
   ChainShape s;
   const int64_t col_vecs = (W + 15) / 16;
   if (n_noise == 0) {
-    s.block = std::min(wg ? wg : (cfg.block ? cfg.block : 256), 256);
+    int block = wg ? wg : (cfg.block ? cfg.block : 256);
+    int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
+    if (block > 256) {  // compiled for at most 256 threads: keep threads per SM
+      cps = std::max(1, cps * block / 256);
+      block = 256;
+    }
+    s.block = block;
     s.unroll = cfg.unroll ? cfg.unroll : 4;
     s.blocked = true;
     const int64_t groups = (rows + s.unroll - 1) / s.unroll;
-    s.rows_parallel = std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)kMaxChainGrid * s.block / col_vecs));
+    const int64_t max_ctas = std::min<int64_t>((int64_t)(reduce ? 2 : 8) * sms * cps, kMaxChainGrid);
+    s.rows_parallel = std::max<int64_t>(1, std::min<int64_t>(groups, max_ctas * s.block / col_vecs));
     s.grid = (int)((s.rows_parallel * col_vecs + s.block - 1) / s.block);
     return s;
   }
@@ -842,7 +850,8 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
     a.partials = ws.partials;
     a.ticket = ws.ticket;
   }
-  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true);
+  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true,
+                                   a.reduce != RED_NONE);
   if (s.grid > kMaxChainGrid) return fail(MRW_ERR_UNSUPPORTED, "chain grid above %d CTAs", kMaxChainGrid);
   s.apply(a);
   CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
@@ -1100,7 +1109,8 @@ mrw_status enqueue_image_overlapped(Launch &L, const Group &g, const View &vin, 
     a.out = (uint8_t *)dout + r0 * pitch;
     a.rows = nr;
     a.row0 = r0;
-    const ChainShape s = chain_shape(cfg, L.sms, geo.W, nr, wg, count_noise(g.pre), a.mirror != 0, true);
+    const ChainShape s = chain_shape(cfg, L.sms, geo.W, nr, wg, count_noise(g.pre), a.mirror != 0, true,
+                                     a.reduce != RED_NONE);
     s.apply(a);
     CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
     CU(cudaEventRecord(ev_k, L.stream));
@@ -1222,7 +1232,7 @@ void prepare_chain(const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, 
   a.mirror = mirror_parity(g.pre);
   fill_ops(g.pre, a.mirror, a.ops);
   pr->n_noise = count_noise(g.pre);
-  pr->cs = chain_shape(cfg, sms, geo.W, geo.rows, wg, pr->n_noise, a.mirror != 0, true);
+  pr->cs = chain_shape(cfg, sms, geo.W, geo.rows, wg, pr->n_noise, a.mirror != 0, true, g.reduce != RED_NONE);
   pr->cs.apply(a);
 }
 
@@ -2173,7 +2183,8 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
           << ",\"grid\":" << std::min<int64_t>(tx * ty * geo.D, (int64_t)sms * s.cps) << ",\"block\":256"
           << ",\"smem\":" << s.smem;
       } else {
-        const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg, count_noise(g.pre));
+        const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg, count_noise(g.pre), false, false,
+                                         g.reduce != RED_NONE);
         o << "\"kernel\":\"chain\",\"ops\":";
         ops_json(o, g.pre);
         o << ",\"reduce_only\":" << (g.reduce_only ? "true" : "false") << ",\"reduce\":" << g.reduce
