@@ -429,6 +429,405 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(const __grid_constant__
   }
 }
 
+// ---- Row-streaming blur kernel --------------------------------------------------------------
+//
+// Groups of the form (pointwise prefix, 5x5 blur) with at most kMaxNoisePerGroup noise stages
+// and no suffix — the batched Filter Pipeline + blur among them — run here instead of through
+// the 2-D tile kernel above. Each warp is an independent worker:
+//   * a work item is a strip of kRowsStrip (124) output columns by tile_h rows of one plane;
+//     lane l owns the 4 blur-input (Q) columns x0 - 2 + 4l .. x0 + 1 + 4l and, for l < 31, the 4
+//     output columns x0 + 4l .. x0 + 3 + 4l;
+//   * the warp streams the item's source rows through a ring of kRowsBufs TMA boxes of
+//     kRowsBoxW x kRowsChunk bytes in its own slice of shared memory, issued ahead by lane 0;
+//   * per source row, each lane applies the prefix to its 4 pixels in registers, takes the two
+//     Q columns right of its quad from lane l + 1 (one shuffle) and forms the horizontal 5-sums of
+//     its 4 output columns in packed 16-bit lanes; a 5-row window of those sums in registers gives
+//     the vertical sums, so every source row is read and transformed once per item;
+//   * edge replication: a lane whose quad crosses the image's left or right edge reads clamped
+//     columns; rows above the image repeat the first row's sums and rows below repeat the last's.
+// Items are claimed from the global tile counter; within an instance the strips of one row band
+// are consecutive, so neighbouring strips write their shared 32-byte sectors at about the same
+// time.
+constexpr int kRowsBufs = 4;
+constexpr int kRowsFifo = kRowsBufs + 2;
+constexpr int kRowsWarps = 8;
+constexpr int kRowsBlock = 32 * kRowsWarps;
+constexpr uint32_t kRowsBoxBytes = (uint32_t)(kRowsBoxW * kRowsChunk);
+
+// A work item, decoded by the warp's issuer and read by its consumer.
+struct RowItem {
+  int64_t out_off;
+  int32_t inst, z, x0, ys, ye, W, H, pitch_out, qa, nchunks, bx;
+  uint32_t seed_xor;
+};
+
+// Issue-side state of a warp (lane 0 writes it, every lane may read it).
+struct RowIssue {
+  int32_t item;   // FIFO slot of the item being issued (-1: none)
+  int32_t j;      // next chunk of that item
+  int32_t count;  // chunks issued so far
+  int32_t tail;   // FIFO slots written so far
+  int32_t done;   // the tile counter is exhausted
+  int32_t pad[3];
+};
+
+struct alignas(128) RowWarpSmem {
+  uint8_t buf[kRowsBufs][kRowsChunk][kRowsBoxW];
+  uint64_t bar[kRowsBufs];
+  RowItem fifo[kRowsFifo];
+  RowIssue iss;
+};
+
+// Index of the last instance whose first tile is <= t (all lanes; ninst >= 1). Each round the 32
+// lanes probe evenly spaced prefix entries of the remaining range and a ballot keeps one stride.
+__device__ __forceinline__ int warp_find_instance(const int64_t *prefix, int ninst, int64_t t, int lane) {
+  int lo = 0, hi = ninst;  // prefix[lo] <= t < prefix[hi]
+  while (hi - lo > 1) {
+    const int span = hi - lo;
+    const int step = (span + 31) >> 5;
+    const int idx = lo + lane * step;
+    const bool le = idx < hi && __ldg(prefix + idx) <= t;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, le);
+    const int k = 31 - __clz((int)m);  // lane 0 always qualifies
+    lo = lo + k * step;
+    hi = min(lo + step, hi);
+  }
+  return lo;
+}
+
+// Claim one more chunk into the ring (all lanes call it; lane 0 writes and issues).
+template <bool MIR>
+__device__ __noinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, int lane) {
+  RowIssue st = w.iss;
+  if (st.done) return;
+  if (st.item < 0 || st.j == w.fifo[st.item % kRowsFifo].nchunks) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.queue, 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    RowItem it;
+    if ((int64_t)t >= a.total_tiles) {
+      it.inst = -1;
+      st.done = 1;
+    } else {
+      const int i = warp_find_instance(a.tile_prefix, a.ninst, (int64_t)t, lane);
+      const StencilInstance in = a.inst[i];
+      const int64_t lt = (int64_t)t - a.tile_prefix[i];
+      const int64_t per_plane = (int64_t)in.tiles_x * in.tiles_y;
+      const int z = (int)(lt / per_plane);
+      const int rem = (int)(lt - (int64_t)z * per_plane);
+      const int seg = rem / in.tiles_x, strip = rem - seg * in.tiles_x;
+      it.inst = i;
+      it.z = z;
+      it.x0 = strip * kRowsStrip;
+      it.ys = seg * a.tile_h;
+      it.ye = min(it.ys + a.tile_h, in.H);
+      it.W = in.W;
+      it.H = in.H;
+      it.pitch_out = in.pitch_out;
+      it.out_off = in.out_off;
+      it.seed_xor = in.seed_xor;
+      it.qa = max(it.ys - 2, 0);
+      const int qb = min(it.ye + 2, in.H);
+      it.nchunks = (qb - it.qa + kRowsChunk - 1) / kRowsChunk;
+      it.bx = MIR ? ((in.W - it.x0 - 126) & ~15) : ((it.x0 - 2) & ~15);
+    }
+    if (lane == 0) w.fifo[st.tail % kRowsFifo] = it;
+    st.item = st.tail;
+    st.tail += 1;
+    st.j = 0;
+    if (st.done) {
+      if (lane == 0) w.iss = st;
+      __syncwarp();
+      return;
+    }
+  }
+  const RowItem &it = w.fifo[st.item % kRowsFifo];
+  if (lane == 0) {
+    const int b = st.count % kRowsBufs;
+    fence_proxy_async();
+    mbar_expect_tx(&w.bar[b], kRowsBoxBytes);
+    tma_load_3d(&w.buf[b][0][0], a.maps + it.inst, it.bx, it.qa + st.j * kRowsChunk, it.z, &w.bar[b]);
+  }
+  st.j += 1;
+  st.count += 1;
+  if (lane == 0) w.iss = st;
+  __syncwarp();
+}
+
+// One pixel of the noise stage, clamp(p + (h mod 41) - 20, 0, 255) with h = F(colpre ^ ypre), written
+// as max(min(p + r, 275) - 20, 0): each bound takes one add-and-compare instruction.
+__device__ __forceinline__ uint32_t noise_px(uint32_t p, uint32_t colpre, uint32_t ypre) {
+  const uint32_t h = fmix32_tail(colpre ^ ypre);
+  const uint32_t r = h % 41u;
+  return (uint32_t)__viaddmax_s32(__viaddmin_s32((int)p, (int)r, 275), -20, 0);
+}
+
+__device__ __forceinline__ uint32_t noise4(uint32_t q, const uint32_t (&c)[4], uint32_t ypre) {
+  const uint32_t r0 = noise_px(q & 0xFFu, c[0], ypre);
+  const uint32_t r1 = noise_px(__byte_perm(q, 0, 0x4441), c[1], ypre);
+  const uint32_t r2 = noise_px(__byte_perm(q, 0, 0x4442), c[2], ypre);
+  const uint32_t r3 = noise_px(q >> 24, c[3], ypre);
+  return r0 + r1 * 0x100u + r2 * 0x10000u + r3 * 0x1000000u;  // bytes: the adds do not carry
+}
+
+// Prefix ops on the 4 Q pixels of a lane (word byte k = Q column c0 + k); cpa / cpb hold the
+// column hash halves of the first and second noise op.
+template <int NN>
+__device__ __forceinline__ uint32_t rows_prefix(const StencilArgs &a, uint32_t q, const uint32_t (&cpa)[4],
+                                                const uint32_t (&cpb)[4], uint32_t ypre) {
+  int kn = 0;
+  for (int i = 0; i < a.npre; ++i) {
+    const int kind = a.pre[i].kind;
+    if (kind == OP_SOLARISE) {
+      q = solarise4(q);
+    } else if (kind == OP_THRESH) {
+      const uint32_t t = a.pre[i].t;
+      const uint32_t t0 = (t & 0xFFu) * 0x01010101u, t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
+      q = (ge4(q, t0, t0 & 0x7F7F7F7Fu) >> 7) + (ge4(q, t1, t1 & 0x7F7F7F7Fu) >> 7);
+    } else if (kind == OP_NOISE) {
+      if constexpr (NN >= 1) {
+        if (kn == 0) {
+          q = noise4(q, cpa, ypre);
+        } else {
+          if constexpr (NN >= 2) q = noise4(q, cpb, ypre);
+        }
+      }
+      ++kn;
+    }
+  }
+  return q;
+}
+
+// Bounded wait of the whole warp on chunk s's barrier; the result is the same on every lane.
+__device__ __forceinline__ bool rows_wait(RowWarpSmem &w, int s, uint32_t polls) {
+  const bool ok = mbar_wait_bounded(&w.bar[s % kRowsBufs], (uint32_t)(s / kRowsBufs) & 1u, polls);
+  return __all_sync(0xFFFFFFFFu, ok);
+}
+
+// Per-lane state of the item being consumed: only what the row loop needs stays in registers.
+struct RowLane {
+  uint8_t *orow;     // this lane's output quad in the next output row
+  int32_t pitch_out;
+  int32_t wi;        // first of the two 32-bit words of a box row that hold the lane's 4 Q pixels
+  uint32_t sel;      // byte_perm selector picking the 4 Q pixels out of those 8 bytes (reversed
+                     // for a mirrored prefix, edge columns replicated)
+  int32_t nout;      // output bytes of the lane's quad (0: none)
+  uint32_t yrow;     // global row (plane * H + row) of the item's first source row, for the hash
+};
+
+// The lane's 4 Q pixels of one box row (Q column c0 + k in byte k).
+__device__ __forceinline__ uint32_t rows_quad(const uint8_t *row, const RowLane &L) {
+  const uint32_t *r32 = reinterpret_cast<const uint32_t *>(row) + L.wi;
+  return __byte_perm(r32[0], r32[1], L.sel);
+}
+
+// Prefix ops on the lane's quads of G consecutive source rows (row j's hash row is y0 + j): each
+// op is decoded once for the G rows, whose 4 G pixels are independent work for the scheduler.
+template <int NN, int G>
+__device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q)[G], const uint32_t (&cpa)[4],
+                                              const uint32_t (&cpb)[4], uint32_t y0) {
+  uint32_t yp[G];
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const uint32_t y = y0 + (uint32_t)j;
+    yp[j] = y ^ (y >> 16);
+  }
+  int kn = 0;
+  for (int i = 0; i < a.npre; ++i) {
+    const int kind = a.pre[i].kind;
+    if (kind == OP_SOLARISE) {
+#pragma unroll
+      for (int j = 0; j < G; ++j) q[j] = solarise4(q[j]);
+    } else if (kind == OP_THRESH) {
+      const uint32_t t = a.pre[i].t;
+      const uint32_t t0 = (t & 0xFFu) * 0x01010101u, t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        q[j] = (ge4(q[j], t0, t0 & 0x7F7F7F7Fu) >> 7) + (ge4(q[j], t1, t1 & 0x7F7F7F7Fu) >> 7);
+    } else if (kind == OP_NOISE) {
+      if constexpr (NN >= 1) {
+        if (kn == 0) {
+#pragma unroll
+          for (int j = 0; j < G; ++j) q[j] = noise4(q[j], cpa, yp[j]);
+        } else {
+          if constexpr (NN >= 2) {
+#pragma unroll
+            for (int j = 0; j < G; ++j) q[j] = noise4(q[j], cpb, yp[j]);
+          }
+        }
+      }
+      ++kn;
+    }
+  }
+}
+
+// Rows of source data a lane transforms together (two groups per TMA box).
+constexpr int kRowsGroup = 4;
+static_assert(kRowsChunk % kRowsGroup == 0, "a row group must not straddle two boxes");
+
+// MINB: CTAs per SM the registers are budgeted for (4: 64 registers; 3: 80).
+template <int NN, bool MIR, int MINB>
+__global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __grid_constant__ StencilArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  RowWarpSmem &w = reinterpret_cast<RowWarpSmem *>(smem)[threadIdx.x >> 5];
+  const uint32_t polls = a.wait_polls ? a.wait_polls - 1 : kWaitPolls;
+
+  if (lane == 0) {
+    for (int b = 0; b < kRowsBufs; ++b) mbar_init(&w.bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    RowIssue st{};
+    st.item = -1;
+    w.iss = st;
+  }
+  __syncwarp();
+  for (int k = 0; k < kRowsBufs; ++k) rows_issue<MIR>(a, w, lane);
+
+  int cur = 0;   // boxes consumed so far
+  int head = 0;  // FIFO slots consumed so far
+  bool failed = false;
+  while (true) {
+    const RowItem &it = w.fifo[head % kRowsFifo];
+    ++head;
+    if (it.inst < 0) break;
+    uint32_t cpa[4] = {0, 0, 0, 0}, cpb[4] = {0, 0, 0, 0};
+    RowLane L;
+    int nfresh, topdup, botdup;
+    {
+      const int W = it.W;
+      const int c0 = it.x0 - 2 + 4 * lane;
+      // column halves of the noise hashes of this lane's (clamped) Q columns
+      if constexpr (NN > 0) {
+        int kn = 0;
+        for (int i = 0; i < a.npre && kn < NN; ++i) {
+          if (a.pre[i].kind != OP_NOISE) continue;
+          const uint32_t fs = fmix32(a.pre[i].seed ^ it.seed_xor);
+          const int flip = a.pre[i].flip;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int cc = min(max(c0 + k, 0), W - 1);
+            const uint32_t c = fmix32(fs ^ (uint32_t)(flip ? W - 1 - cc : cc));
+            if (kn == 0) cpa[k] = c ^ (c >> 16);
+            if constexpr (NN >= 2) {
+              if (kn == 1) cpb[k] = c ^ (c >> 16);
+            }
+          }
+          ++kn;
+        }
+      }
+      // box offsets of the 4 (clamped, possibly mirrored) source columns; they span at most 4
+      // consecutive bytes, which lie in the two words from word `wi` on
+      int off[4], lo = 1 << 30;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int cc = min(max(c0 + k, 0), W - 1);
+        off[k] = (MIR ? W - 1 - cc : cc) - it.bx;
+        lo = min(lo, off[k]);
+      }
+      L.wi = lo >> 2;
+      L.sel = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) L.sel |= (uint32_t)(off[k] - 4 * L.wi) << (4 * k);
+      const int xo = it.x0 + 4 * lane;
+      L.nout = lane < 31 ? max(0, min(4, W - xo)) : 0;
+      L.pitch_out = it.pitch_out;
+      L.orow = a.out_base + it.out_off + ((int64_t)it.z * it.H + it.ys) * it.pitch_out + xo;
+      L.yrow = (uint32_t)it.z * (uint32_t)it.H + (uint32_t)it.qa;
+      const int qb = min(it.ye + 2, it.H);
+      nfresh = qb - it.qa;                // source rows the item reads, qa .. qb - 1
+      topdup = it.qa - (it.ys - 2);       // rows above the image: copies of row 0
+      botdup = it.ye + 2 - qb;            // rows below the image: copies of row H - 1
+    }
+
+    if (!rows_wait(w, cur, polls)) {
+      failed = true;
+      break;
+    }
+    // 5-row window of horizontal sums (oldest first) for output columns (0, 2) and (1, 3), and
+    // its running sums plus 12 (round half up in (sum + 12) / 25)
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
+    uint32_t s02 = 0x000C000Cu, s13 = 0x000C000Cu;
+    int pushed = 0;  // virtual rows entered into the window so far
+    // enter one virtual row; from the fifth on, the window's sums give an output row
+    auto push = [&](uint32_t x02, uint32_t x13, bool full) {
+      s02 = s02 + x02 - a0;
+      s13 = s13 + x13 - b0;
+      a0 = a1; a1 = a2; a2 = a3; a3 = a4; a4 = x02;
+      b0 = b1; b1 = b2; b2 = b3; b3 = b4; b4 = x13;
+      if (full || ++pushed >= 5) {
+        if (L.nout > 0) {
+          // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane: high lane mulhi(s, 5243) >> 1,
+          // low lane the same on s << 16 (exact over the whole range of both lanes)
+          const uint32_t d0 = __umulhi(s02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(s02, 5243u) >> 1;
+          const uint32_t d1 = __umulhi(s13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(s13, 5243u) >> 1;
+          store4(L.orow, d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u, L.nout);
+        }
+        L.orow += L.pitch_out;
+      }
+    };
+    for (int r0 = 0; r0 < nfresh; r0 += kRowsGroup) {
+      if (r0 > 0 && (r0 % kRowsChunk) == 0) {
+        __syncwarp();
+        ++cur;
+        rows_issue<MIR>(a, w, lane);
+        if (!rows_wait(w, cur, polls)) {
+          failed = true;
+          break;
+        }
+      }
+      const uint8_t *box = &w.buf[cur % kRowsBufs][r0 % kRowsChunk][0];
+      uint32_t q[kRowsGroup];
+#pragma unroll
+      for (int j = 0; j < kRowsGroup; ++j) q[j] = rows_quad(box + j * kRowsBoxW, L);
+      rows_prefix_g<NN, kRowsGroup>(a, q, cpa, cpb, L.yrow + (uint32_t)r0);
+      uint32_t h02[kRowsGroup], h13[kRowsGroup];
+#pragma unroll
+      for (int j = 0; j < kRowsGroup; ++j) {
+        const uint32_t nb = __shfl_down_sync(0xFFFFFFFFu, q[j], 1);
+        // horizontal 5-sums of output columns 0..3 (Q bytes k .. k + 4 of q:nb), packed as
+        // (0, 2) and (1, 3) in 16-bit lanes
+        const uint32_t E = __byte_perm(q[j], 0, 0x4240), O = __byte_perm(q[j], 0, 0x4341);
+        const uint32_t E2 = __byte_perm(nb, 0, 0x4240), O2 = __byte_perm(nb, 0, 0x4341);
+        const uint32_t A = E + O, A2 = E2 + O2, P = __byte_perm(A, A2, 0x5432);
+        h02[j] = A + P + E2;
+        h13[j] = O + P + A2;
+      }
+      if (r0 == 0 && topdup > 0) {  // rows above the image repeat row 0
+        a3 = a4 = h02[0];
+        b3 = b4 = h13[0];
+        s02 += 2 * h02[0];
+        s13 += 2 * h13[0];
+        pushed = topdup;
+      }
+      if (pushed >= 4 && r0 + kRowsGroup <= nfresh) {
+        // steady state: every row of the group completes an output row
+#pragma unroll
+        for (int j = 0; j < kRowsGroup; ++j) push(h02[j], h13[j], true);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kRowsGroup; ++j)
+          if (r0 + j < nfresh) push(h02[j], h13[j], false);
+      }
+    }
+    if (failed) break;
+    for (int d = 0; d < botdup; ++d) push(a4, b4, false);  // rows below the image repeat row H - 1
+    __syncwarp();
+    ++cur;
+    rows_issue<MIR>(a, w, lane);
+  }
+
+  if (failed) {
+    if (lane == 0) {
+      *(volatile unsigned int *)a.status = 1u;  // may be mapped host memory
+      // let this warp's copies in flight land before it leaves (bounded as well)
+      const int issued = w.iss.count;
+      for (int s = cur; s < issued; ++s)
+        (void)mbar_wait_bounded(&w.bar[s % kRowsBufs], (uint32_t)(s / kRowsBufs) & 1u);
+    }
+    __syncwarp();
+  }
+}
+
 const void *stencil_fn(int tile_w, int halo) {
   if (halo == 2) {
     switch (tile_w) {
@@ -477,6 +876,35 @@ size_t stencil_smem_bytes(int tile_h, int tile_w, int halo) {
   return b + 2 * sizeof(uint64_t);
 }
 
+namespace {
+template <int MINB>
+const void *stencil_rows_fn_b(int n_noise, int mirror) {
+  switch (n_noise * 2 + (mirror ? 1 : 0)) {
+    case 0: return (const void *)stencil_rows_kernel<0, false, MINB>;
+    case 1: return (const void *)stencil_rows_kernel<0, true, MINB>;
+    case 2: return (const void *)stencil_rows_kernel<1, false, MINB>;
+    case 3: return (const void *)stencil_rows_kernel<1, true, MINB>;
+    case 4: return (const void *)stencil_rows_kernel<2, false, MINB>;
+    case 5: return (const void *)stencil_rows_kernel<2, true, MINB>;
+    default: return nullptr;
+  }
+}
+
+// The variant budgeted for 4 CTAs per SM serves requests of 4 or more, the other fewer.
+const void *stencil_rows_fn(int n_noise, int mirror, int cps) {
+  return cps >= 4 ? stencil_rows_fn_b<4>(n_noise, mirror) : stencil_rows_fn_b<3>(n_noise, mirror);
+}
+
+int count_noise_ops(const ChainOp *ops, int n) {
+  int c = 0;
+  for (int i = 0; i < n; ++i) c += ops[i].kind == OP_NOISE;
+  return c;
+}
+}  // namespace
+
+size_t stencil_rows_smem_bytes() { return sizeof(RowWarpSmem) * kRowsWarps; }
+int stencil_rows_block() { return kRowsBlock; }
+
 cudaError_t stencil_prepare() {
   static bool attr_set = false;
   if (!attr_set) {
@@ -485,18 +913,47 @@ cudaError_t stencil_prepare() {
         cudaError_t e = cudaFuncSetAttribute(stencil_fn(w, h), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
       }
+    for (int v = 0; v < 12; ++v) {
+      cudaError_t e = cudaFuncSetAttribute(stencil_rows_fn((v >> 1) % 3, v & 1, v < 6 ? 4 : 3),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_rows_smem_bytes());
+      if (e != cudaSuccess) return e;
+    }
     attr_set = true;
   }
   return cudaSuccess;
 }
 
+int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps) {
+  static int cache[3][2][2] = {};
+  if (n_noise < 0 || n_noise > 2) return 1;
+  int &c = cache[n_noise][mirror ? 1 : 0][cps >= 4 ? 1 : 0];
+  if (c) return c;
+  int nb = 0;
+  if (stencil_prepare() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stencil_rows_fn(n_noise, mirror, cps), kRowsBlock,
+                                                    stencil_rows_smem_bytes()) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  c = nb > 0 ? nb : 1;
+  return c;
+}
+
 cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-  if (block != kBlock || smem > 200 * 1024 || stencil_tile_width(a.tile_w) != a.tile_w ||
-      (a.halo != 0 && a.halo != 2))
-    return cudaErrorInvalidValue;
   cudaError_t e = stencil_prepare();
   if (e != cudaSuccess) return e;
   void *args[] = {(void *)&a};
+  if (a.rows_kernel) {
+    const int nn = count_noise_ops(a.pre, a.npre);
+    if (!stencil_rows_eligible(a.halo, a.nsuf, a.msuf, nn) || block != kRowsBlock ||
+        smem != stencil_rows_smem_bytes() || a.tile_w != kRowsStrip || a.box_w != kRowsBoxW ||
+        a.box_h != kRowsChunk || a.tile_h < 1)
+      return cudaErrorInvalidValue;
+    return cudaLaunchKernel(stencil_rows_fn(nn, a.mpre, a.rows_cps), dim3(grid), dim3(block), args, smem, s);
+  }
+  if (block != kBlock || smem > 200 * 1024 || stencil_tile_width(a.tile_w) != a.tile_w ||
+      (a.halo != 0 && a.halo != 2))
+    return cudaErrorInvalidValue;
   return cudaLaunchKernel(stencil_fn(a.tile_w, a.halo), dim3(grid), dim3(block), args, smem, s);
 }
 

@@ -859,20 +859,14 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
 }
 
 struct StencilShape {
-  int tile_h, tile_w, box_w, box_h, cps;
+  int tile_h, tile_w, box_w, box_h, cps, block;
   size_t smem;
 };
 
-StencilShape stencil_shape(const mrw_config &cfg, int halo) {
-  StencilShape s;
-  s.tile_h = cfg.tile_rows ? std::min(cfg.tile_rows, 252 - 2 * halo) : 32;
-  s.tile_w = stencil_tile_width(cfg.tile_cols ? cfg.tile_cols : 128);
-  s.tile_h = std::max(1, s.tile_h);
-  s.box_w = (int)round_up(s.tile_w + 2 * halo + 15, 16);
-  s.box_h = s.tile_h + 2 * halo;
-  s.cps = std::min(8, cfg.ctas_per_sm ? cfg.ctas_per_sm : 4);
-  s.smem = stencil_smem_bytes(s.tile_h, s.tile_w, halo);
-  return s;
+// A stencil group runs on the row-streaming kernel when it has a blur, no suffix and at most
+// kMaxNoisePerGroup noise stages before the blur; otherwise on the 2-D tile kernel.
+bool group_rows(const Group &g) {
+  return stencil_rows_eligible(g.blur ? 2 : 0, (int)g.suf.size(), mirror_parity(g.suf), count_noise(g.pre));
 }
 
 void fill_stencil_ops(const Group &g, StencilArgs &a) {
@@ -882,8 +876,54 @@ void fill_stencil_ops(const Group &g, StencilArgs &a) {
   a.nsuf = (int32_t)g.suf.size();
   a.mpre = mirror_parity(g.pre);
   a.msuf = mirror_parity(g.suf);
+  a.rows_kernel = group_rows(g) ? 1 : 0;
   fill_ops(g.pre, a.mpre, a.pre);
   fill_ops(g.suf, a.msuf, a.suf);
+}
+
+// Launch shape of a stencil group. The 2-D tile kernel takes tile_rows x tile_cols output tiles.
+// The row-streaming kernel takes strips of kRowsStrip columns by 4 x tile_rows rows (a work item
+// of one warp; the 4 halo rows it re-reads cost 4 / (4 x tile_rows) of the item).
+StencilShape stencil_shape(const mrw_config &cfg, const StencilArgs &a) {
+  StencilShape s;
+  const int halo = a.halo;
+  if (a.rows_kernel) {
+    int nn = 0;
+    for (int i = 0; i < a.npre; ++i) nn += a.pre[i].kind == OP_NOISE;
+    s.tile_h = std::min(4096, std::max(8, 4 * (cfg.tile_rows ? cfg.tile_rows : 32)));
+    s.tile_w = kRowsStrip;
+    s.box_w = kRowsBoxW;
+    s.box_h = kRowsChunk;
+    const int want = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
+    s.cps = std::max(1, std::min(want, stencil_rows_blocks_per_sm(nn, a.mpre, want)));
+    s.block = stencil_rows_block();
+    s.smem = stencil_rows_smem_bytes();
+    return s;
+  }
+  s.tile_h = cfg.tile_rows ? std::min(cfg.tile_rows, 252 - 2 * halo) : 32;
+  s.tile_w = stencil_tile_width(cfg.tile_cols ? cfg.tile_cols : 128);
+  s.tile_h = std::max(1, s.tile_h);
+  s.box_w = (int)round_up(s.tile_w + 2 * halo + 15, 16);
+  s.box_h = s.tile_h + 2 * halo;
+  s.cps = std::min(8, cfg.ctas_per_sm ? cfg.ctas_per_sm : 4);
+  s.block = 256;
+  s.smem = stencil_smem_bytes(s.tile_h, s.tile_w, halo);
+  return s;
+}
+
+void apply_shape(StencilArgs &a, const StencilShape &s) {
+  a.rows_cps = s.cps;
+  a.tile_h = s.tile_h;
+  a.tile_w = s.tile_w;
+  a.box_w = s.box_w;
+  a.box_h = s.box_h;
+}
+
+// Persistent grid of a stencil launch over `tiles` work items: one item per CTA (tile kernel) or
+// per warp (row-streaming kernel) at most, and at most cps CTAs per SM.
+int stencil_grid(const StencilShape &s, const StencilArgs &a, int64_t tiles, int sms) {
+  const int64_t per_cta = a.rows_kernel ? s.block / 32 : 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + per_cta - 1) / per_cta, (int64_t)sms * s.cps));
 }
 
 // Device tables of a stencil launch: tensor maps, instances and the tile prefix sum.
@@ -922,7 +962,7 @@ mrw_status run_stencil_single(Launch &L, const Group &g, const uint8_t *in, int6
                               const ImgGeom &geo, const mrw_config &cfg, unsigned int *status) {
   StencilArgs a{};
   fill_stencil_ops(g, a);
-  const StencilShape s = stencil_shape(cfg, a.halo);
+  const StencilShape s = stencil_shape(cfg, a);
   StencilTables t;
   t.maps.resize(1);
   CU(encode_u8_map(&t.maps[0], in, geo.W, geo.H, geo.D, ip, s.box_w, s.box_h));
@@ -940,7 +980,7 @@ mrw_status run_stencil_single(Launch &L, const Group &g, const uint8_t *in, int6
   t.inst.push_back(inst);
   t.total = (int64_t)inst.tiles_x * inst.tiles_y * geo.D;
   t.prefix = {0, t.total};
-  if (t.total >= (int64_t)UINT32_MAX - 1) return fail(MRW_ERR_UNSUPPORTED, "too many tiles");
+  if (t.total >= (int64_t)1 << 31) return fail(MRW_ERR_UNSUPPORTED, "too many tiles");
   void *dm, *di, *dp;
   TRY(upload_tables(L, t, &dm, &di, &dp, false, nullptr));
   void *q;
@@ -955,12 +995,8 @@ mrw_status run_stencil_single(Launch &L, const Group &g, const uint8_t *in, int6
   a.status = status;
   a.total_tiles = t.total;
   a.ninst = 1;
-  a.tile_h = s.tile_h;
-  a.tile_w = s.tile_w;
-  a.box_w = s.box_w;
-  a.box_h = s.box_h;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t.total, (int64_t)L.sms * s.cps));
-  CU(launch_stencil(a, grid, 256, s.smem, L.stream));
+  apply_shape(a, s);
+  CU(launch_stencil(a, stencil_grid(s, a, t.total, L.sms), s.block, s.smem, L.stream));
   return MRW_OK;
 }
 
@@ -1146,7 +1182,7 @@ struct Prepared {
   ChainShape cs{};
   int n_noise = 0;
   StencilArgs sa{};
-  int grid = 0;
+  int grid = 0, block = 256;
   size_t smem = 0;
   unsigned int *queue = nullptr;
 };
@@ -1179,7 +1215,7 @@ mrw_status prepare_stencil(Launch &L, const Group &g, const uint8_t *in, int64_t
                            std::vector<void *> *owned, Prepared *pr) {
   StencilArgs a{};
   fill_stencil_ops(g, a);
-  const StencilShape s = stencil_shape(cfg, a.halo);
+  const StencilShape s = stencil_shape(cfg, a);
   StencilTables t;
   t.maps.resize(1);
   CU(encode_u8_map(&t.maps[0], in, geo.W, geo.H, geo.D, ip, s.box_w, s.box_h));
@@ -1205,13 +1241,11 @@ mrw_status prepare_stencil(Launch &L, const Group &g, const uint8_t *in, int64_t
   a.status = status;
   a.total_tiles = t.total;
   a.ninst = 1;
-  a.tile_h = s.tile_h;
-  a.tile_w = s.tile_w;
-  a.box_w = s.box_w;
-  a.box_h = s.box_h;
+  apply_shape(a, s);
   pr->stencil = true;
   pr->sa = a;
-  pr->grid = (int)std::max<int64_t>(1, std::min<int64_t>(t.total, (int64_t)L.sms * s.cps));
+  pr->grid = stencil_grid(s, a, t.total, L.sms);
+  pr->block = s.block;
   pr->smem = s.smem;
   pr->queue = queue;
   return MRW_OK;
@@ -1301,7 +1335,7 @@ mrw_status build_while_plan(Launch &L, const Program &p, const ImgGeom &geo, con
       const Prepared &pr = prep[gi];
       if (pr.stencil) {
         e1 = cudaMemsetAsync(pr.queue, 0, sizeof(unsigned int), cs);
-        if (e1 == cudaSuccess) e1 = launch_stencil(pr.sa, pr.grid, 256, pr.smem, cs);
+        if (e1 == cudaSuccess) e1 = launch_stencil(pr.sa, pr.grid, pr.block, pr.smem, cs);
       } else {
         e1 = launch_chain(pr.ca, pr.n_noise, pr.cs.unroll, pr.cs.grid, pr.cs.block, cs);
       }
@@ -1964,14 +1998,21 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
   Launch C = L;
   C.stream = cs;
   std::vector<StencilArgs> launches;
-  std::vector<int> grids;
+  std::vector<int> grids, blocks;
   std::vector<size_t> smems;
+  // Instances in decreasing order of pixels, so the persistent workers take the largest first and
+  // the end of the launch is made of small items (longest-first scheduling of the tile queue).
+  std::vector<int64_t> order((size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    return desc[5 * x + 1] * desc[5 * x + 2] > desc[5 * y + 1] * desc[5 * y + 2];
+  });
   const uint8_t *src = in_arena;
   for (size_t gi = 0; gi < gs.size(); ++gi) {
     const Group &g = gs[gi];
     StencilArgs a{};
     fill_stencil_ops(g, a);
-    const StencilShape s = stencil_shape(cfg, a.halo);
+    const StencilShape s = stencil_shape(cfg, a);
     uint8_t *dst = gi + 1 == gs.size() ? out_arena : (uint8_t *)bp->tmp_arena[gi & 1];
     StencilTables t;
     t.maps.resize((size_t)n);
@@ -1979,7 +2020,8 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
     t.prefix.resize((size_t)n + 1);
     int64_t tiles = 0;
     for (int64_t i = 0; i < n; ++i) {
-      const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
+      const int64_t d = order[(size_t)i];
+      const int64_t off = desc[5 * d], W = desc[5 * d + 1], H = desc[5 * d + 2], pitch = desc[5 * d + 3];
       const cudaError_t e = encode_u8_map(&t.maps[i], src + off, W, H, 1, pitch, s.box_w, s.box_h);
       if (e != cudaSuccess) {
         cudaStreamDestroy(cs);
@@ -1992,7 +2034,7 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
       in.H = (int32_t)H;
       in.D = 1;
       in.pitch_in = in.pitch_out = (int32_t)pitch;
-      in.seed_xor = (uint32_t)desc[5 * i + 4];
+      in.seed_xor = (uint32_t)desc[5 * d + 4];
       in.tiles_x = (int32_t)((W + s.tile_w - 1) / s.tile_w);
       in.tiles_y = (int32_t)((H + s.tile_h - 1) / s.tile_h);
       in.tile_base = tiles;
@@ -2001,7 +2043,7 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
     }
     t.prefix[n] = tiles;
     t.total = tiles;
-    if (tiles >= (int64_t)UINT32_MAX - 1) {
+    if (tiles >= (int64_t)1 << 31) {
       cudaStreamDestroy(cs);
       return fail(MRW_ERR_UNSUPPORTED, "too many tiles in one batch");
     }
@@ -2020,12 +2062,10 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
     a.status = bp->counters + gs.size();
     a.total_tiles = tiles;
     a.ninst = (int32_t)n;
-    a.tile_h = s.tile_h;
-    a.tile_w = s.tile_w;
-    a.box_w = s.box_w;
-    a.box_h = s.box_h;
+    apply_shape(a, s);
     launches.push_back(a);
-    grids.push_back((int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)L.sms * s.cps)));
+    grids.push_back(stencil_grid(s, a, tiles, L.sms));
+    blocks.push_back(s.block);
     smems.push_back(s.smem);
     src = dst;
   }
@@ -2034,7 +2074,7 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(unsigned int) * (gs.size() + 1), cs);
   for (size_t gi = 0; e == cudaSuccess && gi < launches.size(); ++gi)
-    e = launch_stencil(launches[gi], grids[gi], 256, smems[gi], cs);
+    e = launch_stencil(launches[gi], grids[gi], blocks[gi], smems[gi], cs);
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, graph, 0);
@@ -2172,15 +2212,17 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
       const Group &g = gs[i];
       o << (i ? "," : "") << "{";
       if (g.use_stencil) {
-        const StencilShape s = stencil_shape(c, g.blur ? 2 : 0);
+        StencilArgs sa{};
+        fill_stencil_ops(g, sa);
+        const StencilShape s = stencil_shape(c, sa);
         const int64_t tx = (geo.W + s.tile_w - 1) / s.tile_w, ty = (geo.H + s.tile_h - 1) / s.tile_h;
-        o << "\"kernel\":\"stencil\",\"pre\":";
+        o << "\"kernel\":\"" << (sa.rows_kernel ? "stencil_rows" : "stencil") << "\",\"pre\":";
         ops_json(o, g.pre);
         o << ",\"blur\":" << (g.blur ? "true" : "false") << ",\"suf\":";
         ops_json(o, g.suf);
         o << ",\"tile\":[" << s.tile_h << "," << s.tile_w << "],\"box\":[" << s.box_h << "," << s.box_w
           << "],\"tiles_x\":" << tx << ",\"tiles_y\":" << ty << ",\"tiles\":" << tx * ty * geo.D
-          << ",\"grid\":" << std::min<int64_t>(tx * ty * geo.D, (int64_t)sms * s.cps) << ",\"block\":256"
+          << ",\"grid\":" << stencil_grid(s, sa, tx * ty * geo.D, sms) << ",\"block\":" << s.block
           << ",\"smem\":" << s.smem;
       } else {
         const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg, count_noise(g.pre), false, false,
@@ -2768,11 +2810,8 @@ extern "C" mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t
   a.nsuf = nsuf;
   fill_ops_array(st, npre, a.pre, &a.mpre);
   fill_ops_array(st + npre + (blur_at >= 0 ? 1 : 0), nsuf, a.suf, &a.msuf);
-  const StencilShape s = stencil_shape(c, a.halo);
-  a.tile_h = s.tile_h;
-  a.tile_w = s.tile_w;
-  a.box_w = s.box_w;
-  a.box_h = s.box_h;
+  const StencilShape s = stencil_shape(c, a);
+  apply_shape(a, s);
   int dev = 0, sms = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -97,9 +97,29 @@ struct StencilArgs {
   int32_t reduce;                   // reserved (0)
   uint32_t wait_polls;              // 0: default bound; N > 0: give up a tile wait after N - 1 polls
                                     // (failure-detection tests set it through MRW_TEST_WAIT_POLLS)
+  int32_t rows_kernel;              // 1: the row-streaming blur kernel (see stencil_rows_eligible):
+                                    // tiles are strips of kRowsStrip columns by tile_h rows and the
+                                    // maps' box is kRowsBoxW x kRowsChunk
+  int32_t rows_cps;                 // row-streaming kernel: CTAs per SM the launch is sized for
+                                    // (selects the variant budgeted for 4, or for 3, CTAs per SM)
   ChainOp pre[kMaxChainOps];
   ChainOp suf[kMaxChainOps];
 };
+
+// Row-streaming blur kernel: a warp streams strips of kRowsStrip output columns through a ring of
+// kRowsBoxW x kRowsChunk TMA boxes. It runs groups with a blur, no suffix ops and at most
+// kMaxNoisePerGroup noise stages in the prefix.
+constexpr int kRowsStrip = 124;
+constexpr int kRowsBoxW = 144;
+constexpr int kRowsChunk = 8;
+inline bool stencil_rows_eligible(int halo, int nsuf, int msuf, int n_noise_pre) {
+  return halo == 2 && nsuf == 0 && msuf == 0 && n_noise_pre <= kMaxNoisePerGroup;
+}
+size_t stencil_rows_smem_bytes();
+int stencil_rows_block();
+// Resident CTAs per SM of the row-streaming kernel variant for a request of cps CTAs per SM
+// (occupancy query, cached).
+int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps);
 
 // Tile widths the stencil kernel is compiled for (64, 128, 224): the one a request rounds to.
 int stencil_tile_width(int requested);

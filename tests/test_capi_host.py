@@ -116,13 +116,17 @@ def test_fused_groups_and_unfused_groups(lib):
     pb = mrw.pipeline(mrw.stage("noise", seed=1), mrw.stage("mirror"), mrw.stage("blur5"), mrw.stage("solarise"),
                       mrw.stage("blur5"))
     d = mrw.plan_describe(pb, _image_args(300, 333))
-    assert [x["kernel"] for x in d["groups"]] == ["stencil", "stencil"]
+    # a group with pointwise stages after its blur runs on the 2-D tile kernel; a blur with only a
+    # prefix on the row-streaming kernel, whose work items are strips of 124 columns
+    assert [x["kernel"] for x in d["groups"]] == ["stencil", "stencil_rows"]
     assert d["groups"][0]["pre"] == ["noise", "mirror"] and d["groups"][0]["suf"] == ["solarise"]
     assert d["groups"][1]["pre"] == [] and d["groups"][1]["blur"]
     # stencil tiles cover the plane
     g0 = d["groups"][0]
     assert g0["tiles_x"] * g0["tile"][1] >= 333 and (g0["tiles_x"] - 1) * g0["tile"][1] < 333
     assert g0["tiles_y"] * g0["tile"][0] >= 300 and (g0["tiles_y"] - 1) * g0["tile"][0] < 300
+    g1 = d["groups"][1]
+    assert g1["tile"][1] == 124 and g1["tiles_x"] == 3 and g1["tiles_y"] * g1["tile"][0] >= 300
     # three noise stages do not fit one chain group's registers
     p3 = mrw.pipeline(*[mrw.stage("noise", seed=s) for s in range(3)])
     assert len(mrw.plan_describe(p3, _image_args())["groups"]) == 2

@@ -44,6 +44,28 @@ def test_stencil_prefix_suffix_orders(names):
             assert np.array_equal(got, want), (names, h, w, cfg.as_tuple())
 
 
+@pytest.mark.parametrize("names", [
+    FILTER_BLUR,
+    ["noise", "mirror", "noise", "solarise", "blur5"],
+    ["threshold3", "mirror", "blur5"],
+])
+def test_row_streaming_blur_strip_and_segment_edges(names):
+    # blur groups with only a prefix run on the row-streaming kernel: strips of 124 output columns,
+    # items of 4 x tile_rows rows streamed through 8-row TMA boxes; the shapes put image edges on,
+    # just before and just after strip and item boundaries (tile_rows 2 -> 8-row items, one box each)
+    seeds = {i: 300 + 11 * i for i in range(len(names))}
+    tree = build_image_tree(names, seeds)
+    otree = oracle_tree(names, seeds)
+    for (h, w) in [(129, 124), (127, 125), (64, 123), (65, 248), (200, 249), (257, 372), (6, 4), (4, 6), (9, 130)]:
+        img = inputs.filter_image(h, w, seed=h + w)
+        want, _ = S.evaluate_image(otree, img)
+        for cfg in (M.config(), M.config(tile_rows=16), M.config(tile_rows=2, ctas_per_sm=2)):
+            got, _ = run_image(tree, img, cfg)
+            assert np.array_equal(got, want), (names, h, w, cfg.as_tuple())
+        got, _ = run_image(tree, img, pitch=w + 16 * 9 - w % 16)  # a wider row pitch than needed
+        assert np.array_equal(got, want), (names, h, w, "pitch")
+
+
 def test_every_candidate_tile_shape():
     img = inputs.filter_image(200, 453, seed=9)
     tree = build_image_tree(FILTER_BLUR, {0: 2})
