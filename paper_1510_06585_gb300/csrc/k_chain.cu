@@ -20,30 +20,10 @@
 // MapReduce (Section 2.1; merging function +, Section 3.4) is fused: per-thread counters, warp
 // reduction with redux.sync, block reduction in shared memory, one 64-bit atomic per block.
 #include "mrw_internal.h"
+#include "pixel_ops.cuh"
 
 namespace mrw {
 namespace {
-
-constexpr uint32_t kHi = 0x80808080u;
-constexpr uint32_t kLo7 = 0x7F7F7F7Fu;
-
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return h;
-}
-
-// fmix32(v) with its first xor-shift already applied to v (the caller passes v ^ (v >> 16)).
-__device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return h;
-}
 
 __device__ __forceinline__ uint4 ld16(const uint8_t *p) {
   return __ldcs(reinterpret_cast<const uint4 *>(p));
@@ -74,19 +54,6 @@ __device__ __forceinline__ uint4 load_mirrored(const uint8_t *row, int xo, int W
                     __byte_perm(w0, w1, sel));
 }
 
-__device__ __forceinline__ uint32_t solarise4(uint32_t w) {
-  // p >= 128 -> 255 - p == p ^ 0xFF; the top bit of each byte selects the flip
-  return w ^ (((w >> 7) & 0x01010101u) * 0xFFu);
-}
-
-// Per byte: 0x80 if a >= t, else 0. Setting a's top bits and clearing t's makes the subtraction
-// borrow-free across bytes; its top bit then compares the low 7 bits, and the top bits of a and t
-// decide the rest. tlo = t & 0x7F7F7F7F.
-__device__ __forceinline__ uint32_t ge4(uint32_t a, uint32_t t, uint32_t tlo) {
-  const uint32_t d = (a | kHi) - tlo;
-  return ((a & ~t) | (~(a ^ t) & d)) & kHi;
-}
-
 struct Thresh {
   uint32_t t0, t0lo, t1, t1lo;
 };
@@ -100,21 +67,9 @@ __device__ __forceinline__ Thresh make_thresh(uint32_t t) {
   return h;
 }
 
-__device__ __forceinline__ uint32_t noise_byte(uint32_t p, uint32_t colpre, uint32_t ypre) {
-  const uint32_t h = fmix32_tail(colpre ^ ypre);
-  const int q = (int)p + (int)(h % 41u) - 20;
-  return (uint32_t)min(max(q, 0), 255);
-}
-
 __device__ __forceinline__ void noise16(uint32_t (&w)[4], const uint32_t (&ch)[16], uint32_t ypre) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t b0 = noise_byte(w[j] & 0xFFu, ch[4 * j + 0], ypre);
-    const uint32_t b1 = noise_byte((w[j] >> 8) & 0xFFu, ch[4 * j + 1], ypre);
-    const uint32_t b2 = noise_byte((w[j] >> 16) & 0xFFu, ch[4 * j + 2], ypre);
-    const uint32_t b3 = noise_byte(w[j] >> 24, ch[4 * j + 3], ypre);
-    w[j] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-  }
+  for (int j = 0; j < 4; ++j) w[j] = noise4(w[j], ch[4 * j], ch[4 * j + 1], ch[4 * j + 2], ch[4 * j + 3], ypre);
 }
 
 // Applies the chain to U segments: each op is decoded once and applied to all of them, which also
@@ -157,8 +112,14 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4]
 
 __device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01010101u, 0u); }
 
+// CTAs per SM the registers of a variant are budgeted for: chains with noise keep 16 column hashes
+// per noise op in registers and are ALU-bound, so their occupancy is set by the unroll depth.
+constexpr int chain_min_blocks(int nn, int u) {
+  return nn == 0 ? 1 : (nn == 1 ? (u <= 2 ? 4 : (u == 4 ? 3 : 2)) : (u <= 2 ? 2 : 1));
+}
+
 template <int NN, bool MIR, int U>
-__global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ ChainArgs a) {
+__global__ void __launch_bounds__(256, chain_min_blocks(NN, U)) chain_kernel(const __grid_constant__ ChainArgs a) {
   // grid * block <= 2^30 threads (kMaxChainGrid CTAs of at most 256): 32-bit thread indices
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t cv = (uint32_t)a.col_vecs;

@@ -21,21 +21,13 @@
 #include <mutex>
 
 #include "mrw_internal.h"
+#include "pixel_ops.cuh"
 
 namespace mrw {
 namespace {
 
 constexpr int kBlock = 256;
 constexpr uint32_t kWaitPolls = 1u << 24;
-
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return h;
-}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -139,31 +131,6 @@ __device__ __forceinline__ uint32_t apply_ops_px(const ChainOp *ops, int n, uint
   return p;
 }
 
-// ---- word (4-pixel) ops ----
-constexpr uint32_t kHi = 0x80808080u;
-
-__device__ __forceinline__ uint32_t solarise4(uint32_t w) { return w ^ (((w >> 7) & 0x01010101u) * 0xFFu); }
-
-// 0x80 per byte where a >= t (borrow-free byte compare; tlo = t & 0x7F7F7F7F)
-__device__ __forceinline__ uint32_t ge4(uint32_t a, uint32_t t, uint32_t tlo) {
-  const uint32_t d = (a | kHi) - tlo;
-  return ((a & ~t) | (~(a ^ t) & d)) & kHi;
-}
-
-__device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return h;
-}
-
-__device__ __forceinline__ uint32_t noise_byte(uint32_t p, uint32_t colpre, uint32_t ypre) {
-  const uint32_t h = fmix32_tail(colpre ^ ypre);
-  const int q = (int)p + (int)(h % 41u) - 20;
-  return (uint32_t)min(max(q, 0), 255);
-}
-
 // Ops on the 4 pixels of a word whose columns are c0..c0+3 (clamped columns gc[k] for the hash);
 // colpre[kn] holds the 4 column hashes of noise op kn (already split as c ^ (c >> 16)).
 struct Cols4 {
@@ -195,8 +162,7 @@ __device__ __forceinline__ uint32_t apply_ops_word(const ChainOp *ops, int n, ui
           c[k] = cc ^ (cc >> 16);
         }
       }
-      w = noise_byte(w & 0xFFu, c[0], ypre) | (noise_byte((w >> 8) & 0xFFu, c[1], ypre) << 8) |
-          (noise_byte((w >> 16) & 0xFFu, c[2], ypre) << 16) | (noise_byte(w >> 24, c[3], ypre) << 24);
+      w = noise4(w, c[0], c[1], c[2], c[3], ypre);
       ++kn;
     }
   }
@@ -552,50 +518,6 @@ __device__ __noinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, in
   st.count += 1;
   if (lane == 0) w.iss = st;
   __syncwarp();
-}
-
-// One pixel of the noise stage, clamp(p + (h mod 41) - 20, 0, 255) with h = F(colpre ^ ypre), written
-// as max(min(p + r, 275) - 20, 0): each bound takes one add-and-compare instruction.
-__device__ __forceinline__ uint32_t noise_px(uint32_t p, uint32_t colpre, uint32_t ypre) {
-  const uint32_t h = fmix32_tail(colpre ^ ypre);
-  const uint32_t r = h % 41u;
-  return (uint32_t)__viaddmax_s32(__viaddmin_s32((int)p, (int)r, 275), -20, 0);
-}
-
-__device__ __forceinline__ uint32_t noise4(uint32_t q, const uint32_t (&c)[4], uint32_t ypre) {
-  const uint32_t r0 = noise_px(q & 0xFFu, c[0], ypre);
-  const uint32_t r1 = noise_px(__byte_perm(q, 0, 0x4441), c[1], ypre);
-  const uint32_t r2 = noise_px(__byte_perm(q, 0, 0x4442), c[2], ypre);
-  const uint32_t r3 = noise_px(q >> 24, c[3], ypre);
-  return r0 + r1 * 0x100u + r2 * 0x10000u + r3 * 0x1000000u;  // bytes: the adds do not carry
-}
-
-// Prefix ops on the 4 Q pixels of a lane (word byte k = Q column c0 + k); cpa / cpb hold the
-// column hash halves of the first and second noise op.
-template <int NN>
-__device__ __forceinline__ uint32_t rows_prefix(const StencilArgs &a, uint32_t q, const uint32_t (&cpa)[4],
-                                                const uint32_t (&cpb)[4], uint32_t ypre) {
-  int kn = 0;
-  for (int i = 0; i < a.npre; ++i) {
-    const int kind = a.pre[i].kind;
-    if (kind == OP_SOLARISE) {
-      q = solarise4(q);
-    } else if (kind == OP_THRESH) {
-      const uint32_t t = a.pre[i].t;
-      const uint32_t t0 = (t & 0xFFu) * 0x01010101u, t1 = ((t >> 8) & 0xFFu) * 0x01010101u;
-      q = (ge4(q, t0, t0 & 0x7F7F7F7Fu) >> 7) + (ge4(q, t1, t1 & 0x7F7F7F7Fu) >> 7);
-    } else if (kind == OP_NOISE) {
-      if constexpr (NN >= 1) {
-        if (kn == 0) {
-          q = noise4(q, cpa, ypre);
-        } else {
-          if constexpr (NN >= 2) q = noise4(q, cpb, ypre);
-        }
-      }
-      ++kn;
-    }
-  }
-  return q;
 }
 
 // Bounded wait of the whole warp on chunk s's barrier; the result is the same on every lane.

@@ -1,0 +1,76 @@
+// Per-pixel arithmetic of the u8 image stages, shared by the chain and stencil kernels.
+//
+// Noise stage: p' = clamp(p + (h mod 41) - 20, 0, 255) with h = F(F(F(seed) ^ x) ^ y) and F the
+// MurmurHash3 32-bit finaliser; x, y are the global column and row of the stage's input. The
+// kernels hoist the column part: colpre = c ^ (c >> 16) with c = F(F(seed) ^ x), and
+// ypre = y ^ (y >> 16), so that F(c ^ y) = fmix32_tail(colpre ^ ypre).
+// Solarise: p < 128 ? p : 255 - p. Threshold: (p >= t0) + (p >= t1).
+// Byte arithmetic is SIMD within 32-bit words (byte k of a word = pixel k).
+#pragma once
+
+#include <stdint.h>
+
+namespace mrw {
+
+constexpr uint32_t kHi = 0x80808080u;
+constexpr uint32_t kLo7 = 0x7F7F7F7Fu;
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// fmix32(v) with its first xor-shift already applied to v (the caller passes v ^ (v >> 16)).
+__device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t solarise4(uint32_t w) {
+  // p >= 128 -> 255 - p == p ^ 0xFF; the top bit of each byte selects the flip
+  return w ^ (((w >> 7) & 0x01010101u) * 0xFFu);
+}
+
+// Per byte: 0x80 if a >= t, else 0. Setting a's top bits and clearing t's makes the subtraction
+// borrow-free across bytes; its top bit then compares the low 7 bits, and the top bits of a and t
+// decide the rest. tlo = t & 0x7F7F7F7F.
+__device__ __forceinline__ uint32_t ge4(uint32_t a, uint32_t t, uint32_t tlo) {
+  const uint32_t d = (a | kHi) - tlo;
+  return ((a & ~t) | (~(a ^ t) & d)) & kHi;
+}
+
+// Labels (a >= t0) + (a >= t1) of the 4 bytes of a (t0, t1 replicated into every byte).
+__device__ __forceinline__ uint32_t thresh4(uint32_t a, uint32_t t0, uint32_t t1) {
+  return (ge4(a, t0, t0 & kLo7) >> 7) + (ge4(a, t1, t1 & kLo7) >> 7);
+}
+
+// One pixel of the noise stage, written as max(min(p + r, 275) - 20, 0) with r = h mod 41:
+// each bound is one add-and-compare instruction.
+__device__ __forceinline__ uint32_t noise_px(uint32_t p, uint32_t colpre, uint32_t ypre) {
+  const uint32_t h = fmix32_tail(colpre ^ ypre);
+  const uint32_t r = h % 41u;
+  return (uint32_t)__viaddmax_s32(__viaddmin_s32((int)p, (int)r, 275), -20, 0);
+}
+
+// The noise stage on the 4 pixels of a word; c[k] is pixel k's colpre.
+__device__ __forceinline__ uint32_t noise4(uint32_t q, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t ypre) {
+  const uint32_t r0 = noise_px(q & 0xFFu, c0, ypre);
+  const uint32_t r1 = noise_px(__byte_perm(q, 0, 0x4441), c1, ypre);
+  const uint32_t r2 = noise_px(__byte_perm(q, 0, 0x4442), c2, ypre);
+  const uint32_t r3 = noise_px(q >> 24, c3, ypre);
+  return r0 + r1 * 0x100u + r2 * 0x10000u + r3 * 0x1000000u;  // bytes: the adds do not carry
+}
+
+__device__ __forceinline__ uint32_t noise4(uint32_t q, const uint32_t (&c)[4], uint32_t ypre) {
+  return noise4(q, c[0], c[1], c[2], c[3], ypre);
+}
+
+}  // namespace mrw
