@@ -402,7 +402,23 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n,
         out.update(nbody_workload(M, device, timed, launcher, fused, unfused))
     if "batched" in which:
         out.update(batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n))
+    if "costmodel" in which:
+        out.update(costmodel_workload())
     return out
+
+
+def costmodel_workload(n_train=4000, n_test=500, max_log2=26):
+    """Learned configuration derivation on random compound skeletons: the MLP (the library's own
+    bf16/fp32 forward, backward and Adam kernels) is trained on the exhaustive tuner's timings and
+    its choices on unseen skeletons are scored by regret against the tuner's best."""
+    from paper_1510_06585_gb300 import costmodel as C
+    t0 = time.perf_counter()
+    res, _, _ = C.experiment(n_train, n_test, max_log2=max_log2, epochs=300, reps=3, log=None)
+    r = lambda d: {k: round(v, 4) for k, v in d.items()}
+    return {"costmodel": {"n_train": n_train, "n_test": n_test, "max_log2": max_log2,
+                          "regret_learned": r(res["learned"]), "regret_default": r(res["default_config"]),
+                          "regret_nearest_neighbour": r(res["nearest_neighbour_kb"]),
+                          "train_seconds": res["train_seconds"], "seconds": round(time.perf_counter() - t0, 1)}}
 
 
 def nbody_workload(M, device, timed, launcher, fused, unfused):
@@ -519,8 +535,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrw", choices=["mrw", "reference"])
     ap.add_argument("--no-extras", dest="extras", action="store_false")
-    ap.add_argument("--workloads", default="filter,nbody,batched",
-                    help="comma list of the extra workloads to run (filter, nbody, batched)")
+    ap.add_argument("--workloads", default="filter,nbody,batched,costmodel",
+                    help="comma list of the extra workloads to run (filter, nbody, batched, costmodel)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--filter-sides", default="1024,8192", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
