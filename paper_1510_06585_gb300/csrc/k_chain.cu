@@ -112,10 +112,12 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4]
 
 __device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01010101u, 0u); }
 
-// CTAs per SM the registers of a variant are budgeted for: chains with noise keep 16 column hashes
-// per noise op in registers and are ALU-bound, so their occupancy is set by the unroll depth.
+// CTAs per SM the registers of a variant are budgeted for (at most 64 registers for 4, 80 for 3,
+// 128 for 2). Chains with noise keep 16 column hashes per noise op in registers and are ALU-bound,
+// so their budget follows the unroll depth; chains without noise keep the compiler's own choice
+// (0: no minimum; 60 registers at unroll 4).
 constexpr int chain_min_blocks(int nn, int u) {
-  return nn == 0 ? 1 : (nn == 1 ? (u <= 2 ? 4 : (u == 4 ? 3 : 2)) : (u <= 2 ? 2 : 1));
+  return nn == 0 ? 0 : (nn == 1 ? (u <= 2 ? 4 : (u == 4 ? 3 : 2)) : (u <= 2 ? 2 : 1));
 }
 
 template <int NN, bool MIR, int U>
