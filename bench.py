@@ -273,6 +273,12 @@ def run_mrw(args):
         assert np.array_equal(c.cpu().numpy(), hist), "segmentation counts differ from the histogram"
     t_unfused = time_steps(step_async(unfused_cfg), K, W, world, device)
     drain()
+    # the same bytes moved by a plain device copy (torch's copy kernel, 128 MiB read + 128 MiB
+    # written per step over the same two rotating sets): what one launch of this size can reach
+    def copy_step(i):
+        x, y, _ = sets[i & 1]
+        y.copy_(x)
+    t_copy = time_steps(copy_step, K, W, world, device) / K
     fused_s = t_fused / K
     unfused_s = t_unfused / K
     value = world * SEG_BYTES * K / t_fused / 1e9
@@ -308,6 +314,8 @@ def run_mrw(args):
                      "unit": "GB/s", "frac": round(SEG_BYTES / fused_s / 1e9 / peaks["hbm_gbs"], 4),
                      "traffic": recorded_traffic("k_chain.cu", "segmentation_512cubed_chain"),
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "copy_same_size_gbs": round(2 * 512 ** 3 / t_copy / 1e9, 2),
+                     "frac_of_copy_same_size": round((2 * 512 ** 3 / fused_s) / (2 * 512 ** 3 / t_copy), 4),
                      "note": "achieved = algorithmic bytes / CUDA-event time of the step (one chain-kernel launch per step; the MapReduce finishes inside it)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
                 "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e},

@@ -423,7 +423,10 @@ constexpr uint32_t kRowsBoxBytes = (uint32_t)(kRowsBoxW * kRowsChunk);
 // A work item, decoded by the warp's issuer and read by its consumer.
 struct RowItem {
   int64_t out_off;
-  int32_t inst, z, x0, ys, ye, W, H, pitch_out, qa, nchunks, bx;
+  int32_t inst, z, x0, ys, ye, W, H, pitch_out;
+  int32_t qa;       // image row of the first box row: ys - 2 (may be negative)
+  int32_t nchunks;  // boxes of kRowsChunk rows covering rows ys - 2 .. ye + 1
+  int32_t bx;       // box column origin (multiple of 16)
   uint32_t seed_xor;
 };
 
@@ -492,9 +495,8 @@ __device__ __noinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, in
       it.pitch_out = in.pitch_out;
       it.out_off = in.out_off;
       it.seed_xor = in.seed_xor;
-      it.qa = max(it.ys - 2, 0);
-      const int qb = min(it.ye + 2, in.H);
-      it.nchunks = (qb - it.qa + kRowsChunk - 1) / kRowsChunk;
+      it.qa = it.ys - 2;  // box row 0 = image row ys - 2 (negative rows read the fill value)
+      it.nchunks = (it.ye - it.ys + 4 + kRowsChunk - 1) / kRowsChunk;
       it.bx = MIR ? ((in.W - it.x0 - 126) & ~15) : ((it.x0 - 2) & ~15);
     }
     if (lane == 0) w.fifo[st.tail % kRowsFifo] = it;
@@ -614,7 +616,6 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
     if (it.inst < 0) break;
     uint32_t cpa[4] = {0, 0, 0, 0}, cpb[4] = {0, 0, 0, 0};
     RowLane L;
-    int nfresh, topdup, botdup;
     {
       const int W = it.W;
       const int c0 = it.x0 - 2 + 4 * lane;
@@ -655,53 +656,29 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
       L.pitch_out = it.pitch_out;
       L.orow = a.out_base + it.out_off + ((int64_t)it.z * it.H + it.ys) * it.pitch_out + xo;
       L.yrow = (uint32_t)it.z * (uint32_t)it.H + (uint32_t)it.qa;
-      const int qb = min(it.ye + 2, it.H);
-      nfresh = qb - it.qa;                // source rows the item reads, qa .. qb - 1
-      topdup = it.qa - (it.ys - 2);       // rows above the image: copies of row 0
-      botdup = it.ye + 2 - qb;            // rows below the image: copies of row H - 1
     }
-
-    if (!rows_wait(w, cur, polls)) {
-      failed = true;
-      break;
-    }
-    // 5-row window of horizontal sums (oldest first) for output columns (0, 2) and (1, 3), and
-    // its running sums plus 12 (round half up in (sum + 12) / 25)
-    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
-    uint32_t s02 = 0x000C000Cu, s13 = 0x000C000Cu;
-    int pushed = 0;  // virtual rows entered into the window so far
-    // enter one virtual row; from the fifth on, the window's sums give an output row
-    auto push = [&](uint32_t x02, uint32_t x13, bool full) {
-      s02 = s02 + x02 - a0;
-      s13 = s13 + x13 - b0;
-      a0 = a1; a1 = a2; a2 = a3; a3 = a4; a4 = x02;
-      b0 = b1; b1 = b2; b2 = b3; b3 = b4; b4 = x13;
-      if (full || ++pushed >= 5) {
-        if (L.nout > 0) {
-          // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane: high lane mulhi(s, 5243) >> 1,
-          // low lane the same on s << 16 (exact over the whole range of both lanes)
-          const uint32_t d0 = __umulhi(s02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(s02, 5243u) >> 1;
-          const uint32_t d1 = __umulhi(s13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(s13, 5243u) >> 1;
-          store4(L.orow, d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u, L.nout);
-        }
-        L.orow += L.pitch_out;
-      }
-    };
-    for (int r0 = 0; r0 < nfresh; r0 += kRowsGroup) {
-      if (r0 > 0 && (r0 % kRowsChunk) == 0) {
+    // Virtual row v = box row v = image row ys - 2 + v, for v < nv. Rows above the image take
+    // row 0's horizontal sums (virtual row vtop), rows below it row H - 1's (virtual row vbot).
+    const int nv = it.ye - it.ys + 4;
+    const int vtop = 2 - it.ys, vbot = it.H + 1 - it.ys;
+    // Output row ys + 4k - 4 + j is the 5-row sum of virtual rows 4k - 4 + j .. 4k + j: the suffix
+    // sums of group k - 1 plus the prefix sums of group k, in packed 16-bit lanes (+12: round half up).
+    uint32_t p02[kRowsGroup] = {0, 0, 0, 0}, p13[kRowsGroup] = {0, 0, 0, 0};
+    for (int k = 0; 4 * k < nv; ++k) {
+      if (k > 0 && (k % (kRowsChunk / kRowsGroup)) == 0) {
         __syncwarp();
         ++cur;
         rows_issue<MIR>(a, w, lane);
-        if (!rows_wait(w, cur, polls)) {
-          failed = true;
-          break;
-        }
       }
-      const uint8_t *box = &w.buf[cur % kRowsBufs][r0 % kRowsChunk][0];
+      if (k % (kRowsChunk / kRowsGroup) == 0 && !rows_wait(w, cur, polls)) {
+        failed = true;
+        break;
+      }
+      const uint8_t *box = &w.buf[cur % kRowsBufs][(4 * k) % kRowsChunk][0];
       uint32_t q[kRowsGroup];
 #pragma unroll
       for (int j = 0; j < kRowsGroup; ++j) q[j] = rows_quad(box + j * kRowsBoxW, L);
-      rows_prefix_g<NN, kRowsGroup>(a, q, cpa, cpb, L.yrow + (uint32_t)r0);
+      rows_prefix_g<NN, kRowsGroup>(a, q, cpa, cpb, L.yrow + (uint32_t)(4 * k));
       uint32_t h02[kRowsGroup], h13[kRowsGroup];
 #pragma unroll
       for (int j = 0; j < kRowsGroup; ++j) {
@@ -714,25 +691,64 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
         h02[j] = A + P + E2;
         h13[j] = O + P + A2;
       }
-      if (r0 == 0 && topdup > 0) {  // rows above the image repeat row 0
-        a3 = a4 = h02[0];
-        b3 = b4 = h13[0];
-        s02 += 2 * h02[0];
-        s13 += 2 * h13[0];
-        pushed = topdup;
-      }
-      if (pushed >= 4 && r0 + kRowsGroup <= nfresh) {
-        // steady state: every row of the group completes an output row
+      if (k == 0 && vtop > 0) {  // rows above the image repeat row 0 (virtual row vtop <= 2)
 #pragma unroll
-        for (int j = 0; j < kRowsGroup; ++j) push(h02[j], h13[j], true);
-      } else {
+        for (int j = 0; j < kRowsGroup - 1; ++j)
+          if (j < vtop) {
+            h02[j] = vtop == 1 ? h02[1] : h02[2];
+            h13[j] = vtop == 1 ? h13[1] : h13[2];
+          }
+      }
+      if (4 * k + kRowsGroup - 1 > vbot) {  // rows below the image repeat row H - 1
 #pragma unroll
         for (int j = 0; j < kRowsGroup; ++j)
-          if (r0 + j < nfresh) push(h02[j], h13[j], false);
+          if (4 * k + j > vbot) {
+            h02[j] = j > 0 ? h02[j - 1] : p02[kRowsGroup - 1];
+            h13[j] = j > 0 ? h13[j - 1] : p13[kRowsGroup - 1];
+          }
+      }
+      if (k > 0) {
+        uint32_t o[kRowsGroup];
+        {
+          uint32_t sa = 0x000C000Cu, sb = 0x000C000Cu, ta = 0, tb = 0;
+          uint32_t suf02[kRowsGroup], suf13[kRowsGroup];
+#pragma unroll
+          for (int j = kRowsGroup - 1; j >= 0; --j) {
+            sa += p02[j];
+            sb += p13[j];
+            suf02[j] = sa;
+            suf13[j] = sb;
+          }
+#pragma unroll
+          for (int j = 0; j < kRowsGroup; ++j) {
+            ta += h02[j];
+            tb += h13[j];
+            const uint32_t v02 = suf02[j] + ta, v13 = suf13[j] + tb;
+            // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane: high lane mulhi(v, 5243) >> 1,
+            // low lane the same on v << 16 (exact over the whole range of both lanes)
+            const uint32_t d0 = __umulhi(v02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(v02, 5243u) >> 1;
+            const uint32_t d1 = __umulhi(v13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(v13, 5243u) >> 1;
+            o[j] = d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u;
+          }
+        }
+        const int nrow = min(kRowsGroup, nv - 4 * k);  // output rows of this group (1..4)
+        if (nrow == kRowsGroup && L.nout == 4) {
+#pragma unroll
+          for (int j = 0; j < kRowsGroup; ++j) *reinterpret_cast<uint32_t *>(L.orow + j * L.pitch_out) = o[j];
+        } else if (L.nout > 0) {
+#pragma unroll
+          for (int j = 0; j < kRowsGroup; ++j)
+            if (j < nrow) store4(L.orow + j * L.pitch_out, o[j], L.nout);
+        }
+        L.orow += kRowsGroup * L.pitch_out;
+      }
+#pragma unroll
+      for (int j = 0; j < kRowsGroup; ++j) {
+        p02[j] = h02[j];
+        p13[j] = h13[j];
       }
     }
     if (failed) break;
-    for (int d = 0; d < botdup; ++d) push(a4, b4, false);  // rows below the image repeat row H - 1
     __syncwarp();
     ++cur;
     rows_issue<MIR>(a, w, lane);
