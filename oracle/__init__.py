@@ -15,7 +15,9 @@ Multi-CPU/Multi-GPU Environments"):
 * ``oracle.mlp``      — FP64 forward/backward/Adam of the cost-model MLP
                         (no counterpart in the paper; it stands in for the
                         configuration-derivation step of Section 3.2);
-* ``oracle.partition``— the partitioning constraints of Section 3.1.
+* ``oracle.partition``— the partitioning constraints of Section 3.1;
+* ``oracle.fft``      — forward and inverse DFT of every row, stage after
+                        stage (Section 4, FFT pipelined with its inversion).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import or run anything here. The CUDA product path never

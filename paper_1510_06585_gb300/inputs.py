@@ -22,6 +22,8 @@ N-body) at the sizes this executor is measured on:
                    each instance 256-byte aligned in one arena; instance i's
                    pixels from PCG64(5_000_000 + i), its noise seed 2 + i    (seed 5)
 * random skeletons for the cost model                                        (seed 6)
+* fft signals    : nfft x N complex64, real and imaginary parts uniform in
+                   [-1, 1), drawn in float64 and rounded to float32          (seed 7)
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ SEED_VOLUME = 3
 SEED_NBODY = 4
 SEED_BATCH = 5
 SEED_MODEL = 6
+SEED_FFT = 7
 
 VOLUME_MEANS = (40.0, 128.0, 220.0)
 VOLUME_SD = 15.0
@@ -80,6 +83,17 @@ def nbody(n: int, seed: int = SEED_NBODY):
     v = np.zeros((n, 4), dtype=np.float32)
     a = np.zeros((n, 4), dtype=np.float32)
     return x, v, a
+
+
+def fft_signals(nfft: int, n: int, seed: int = SEED_FFT) -> np.ndarray:
+    """Complex64 array of shape (nfft, n), real and imaginary parts uniform in [-1, 1)."""
+    rng = _rng(seed)
+    re = rng.uniform(-1.0, 1.0, size=(nfft, n)).astype(np.float32)
+    im = rng.uniform(-1.0, 1.0, size=(nfft, n)).astype(np.float32)
+    out = np.empty((nfft, n), dtype=np.complex64)
+    out.real = re
+    out.imag = im
+    return out
 
 
 def round_up(v: int, m: int) -> int:
