@@ -63,7 +63,8 @@ typedef enum mrw_status {
 /* ------------------------------------------------------------------------------------------ */
 /* Data descriptors (Section 2.1 data types; Section 3.4 partitioning features)                */
 /* ------------------------------------------------------------------------------------------ */
-typedef enum mrw_dtype { MRW_U8 = 0, MRW_I32 = 1, MRW_I64 = 2, MRW_F32 = 3, MRW_F64 = 4, MRW_BF16 = 5 } mrw_dtype;
+/* MRW_C64: complex single precision, interleaved (real, imaginary) float32 pairs, 8 bytes. */
+typedef enum mrw_dtype { MRW_U8 = 0, MRW_I32 = 1, MRW_I64 = 2, MRW_F32 = 3, MRW_F64 = 4, MRW_BF16 = 5, MRW_C64 = 6 } mrw_dtype;
 
 /* Where `data` lives. HOST buffers (pageable or pinned) are staged through device memory the
  * executor allocates per call and frees when the call's work is done, the way the paper's
@@ -107,7 +108,11 @@ typedef enum mrw_stage_kind {
   MRW_ST_NBODY_KDK = 6,   /* one kick-drift-kick step: v += dt/2 a; x += dt v; a = a(x);
                              v += dt/2 a (a must hold a(x) on entry)                            */
   /* f32 Map stage (Section 4, Saxpy): y = alpha * x + y on two float32 vectors                 */
-  MRW_ST_SAXPY = 7
+  MRW_ST_SAXPY = 7,
+  /* Complex stages on rows of 65536 MRW_C64 values (Section 4, FFT pipelined with its inversion;
+   * one row = one 512 KB elementary partitioning unit):                                         */
+  MRW_ST_FFT = 8,         /* X[k] = sum_n x[n] exp(-2 pi i n k / N), not normalised              */
+  MRW_ST_IFFT = 9         /* x[n] = (1/N) sum_k X[k] exp(+2 pi i n k / N)                        */
 } mrw_stage_kind;
 
 typedef struct mrw_stage_params {
@@ -208,7 +213,12 @@ void mrw_node_release(mrw_node_t n);
  *     args[2] = int64[3] class counts (THRESHOLD3 last) or int64[1] sum, overwritten;
  *   N-body trees (NBODY_ACCEL, NBODY_KDK, Pipeline/Loop of them): args = x, v, a, each float32
  *     (N, 4), updated in place;
- *   SAXPY: args = x, y (float32, same shape), y updated in place.
+ *   SAXPY: args = x, y (float32, same shape), y updated in place;
+ *   FFT trees (FFT, IFFT, Pipeline/Map/Loop of them): args = x, y, each MRW_C64 of shape
+ *     (nfft, 65536) or (65536), dense rows; y = the stages applied to every row of x in order; y may
+ *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
+ *     transforms in one launch (a 4-CTA cluster per row, the data on chip between transforms);
+ *     FUSE_NONE runs one launch per transform.
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with
  * mrw_future_release). `cfg` may be NULL (tuned or default configuration). */

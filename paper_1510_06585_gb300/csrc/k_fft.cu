@@ -1,0 +1,274 @@
+// FFT stages (Section 4, FFT pipelined with its inversion): forward and inverse DFTs of N = 65536
+// complex float32 values (one 512 KB elementary partitioning unit) per row, several transforms
+// fused in one launch with the data kept on chip between them.
+//
+// Four-step decomposition: the values x[256 a + b] form a 256 x 256 matrix V[a][b] and
+//   X[k1 + 256 k2] = sum_b W_256^(b k2) W_N^(b k1) sum_a V[a][b] W_256^(a k1),   W_M = e^(-2 pi i / M)
+// that is 256-point transforms down the columns (over a), the twiddle W_N^(b k1), 256-point
+// transforms along the rows (over b). Reading the result Y[k1 + 256 k2] as a matrix U[k2][k1]
+// gives the same shape again, so transforms chain.
+//
+// One cluster of 4 CTAs per row: CTA r owns the 64 columns b in [64r, 64r + 64) of V, and after
+// the row transforms the rows k1 in [64r, 64r + 64) of the result - which are the columns
+// [64r, 64r + 64) of U. Column transforms are local to a CTA; between the two halves of a transform
+// each thread pulls the 32 values its row transforms need from the owning CTAs' shared memory
+// (distributed shared memory), between two cluster barriers. A following transform starts from
+// shared memory; only the first reads and the last writes HBM.
+//
+// 256-point transforms: half a warp per line, radix 16 x 16. Thread t reads positions t + 16 m,
+// does a 16-point DFT (radix 4 x 4 in registers), multiplies by W_256^(t k1), transposes through
+// shared memory inside its line, does a second 16-point DFT and writes position t + 16 k2.
+//
+// Shared-memory layouts (8-byte elements, bank-conflict-free for every access pattern used here):
+//   AB (the first transform's input, element (a, j), j = b - 64 r):
+//       a * 64 + (j ^ ((a ^ (a >> 4)) & 15))
+//   BA (everything after the first exchange, element (j, a)):
+//       j * 256 + ((a & 0xF0) | ((a ^ (a >> 4) ^ j) & 15))
+#include <cooperative_groups.h>
+
+#include "mrw_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace mrw {
+namespace {
+
+constexpr int kN = kFftN;          // 65536
+constexpr int kCols = 64;          // columns per CTA
+constexpr int kThreads = 512;      // 16 warps: 32 lines at a time, half a warp each
+constexpr float kC8 = 0.92387953251128675613f;  // cos(pi / 8)
+constexpr float kS8 = 0.38268343236508977173f;  // sin(pi / 8)
+constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1 / 2)
+
+struct FftSmem {
+  float2 d[kN / 4];      // this CTA's quarter of the row (128 KB)
+  float2 tw256[256];     // W_256^e, e < 256 (forward sign)
+  float2 tlo[kCols][16]; // W_N^(b l),      b = 64 r + j, l < 16
+  float2 thi[kCols][16]; // W_N^(16 b h),   h < 16
+};
+
+__device__ __forceinline__ int ab(int a, int j) { return a * kCols + (j ^ ((a ^ (a >> 4)) & 15)); }
+__device__ __forceinline__ int ba(int j, int a) { return j * 256 + ((a & 0xF0) | ((a ^ (a >> 4) ^ j) & 15)); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 conj_if(float2 a, bool c) { return c ? make_float2(a.x, -a.y) : a; }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -s i (the 4-point kernel W_4^s): s = +1 (forward) maps (x, y) to (y, -x)
+template <int S>
+__device__ __forceinline__ float2 rot(float2 a) {
+  return S > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// 4-point DFT of (a, b, c, d) with kernel W_4^(S n k), results in place (index k).
+template <int S>
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+  const float2 z0 = add(a, c), z1 = sub(a, c), z2 = add(b, d), z3 = rot<S>(sub(b, d));
+  a = add(z0, z2);
+  c = sub(z0, z2);
+  b = add(z1, z3);
+  d = sub(z1, z3);
+}
+
+// W_16^(S e) for the exponents the 4 x 4 split needs.
+template <int S>
+__device__ __forceinline__ float2 w16(int e) {
+  const float s = (float)S;
+  switch (e) {
+    case 1: return make_float2(kC8, -s * kS8);
+    case 2: return make_float2(kR2, -s * kR2);
+    case 3: return make_float2(kS8, -s * kC8);
+    case 4: return make_float2(0.f, -s);
+    case 6: return make_float2(-kR2, -s * kR2);
+    case 9: return make_float2(-kC8, s * kS8);
+    default: return make_float2(1.f, 0.f);
+  }
+}
+
+// 16-point DFT with kernel W_16^(S n k) of v[n]; the result X[k] is left in v[4 (k % 4) + k / 4].
+template <int S>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<S>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);  // over n1
+  // now v[4 k1 + n2] = y[k1][n2]; twiddle W_16^(n2 k1)
+#pragma unroll
+  for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<S>(n2 * k1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);  // over n2
+}
+
+__device__ __forceinline__ int dft16_slot(int k) { return 4 * (k & 3) + (k >> 2); }
+
+// Index of line position p in shared memory: a column of the AB layout, or a row of the BA one.
+template <bool AB>
+__device__ __forceinline__ int line_idx(int line, int p) {
+  return AB ? ab(p, line) : ba(line, p);
+}
+
+// Pass 1 of a 256-point transform on values already in registers (v[m] = position t + 16 m): the
+// 16-point DFT and the W_256^(t k1) twiddle; y[k1] is returned in v[dft16_slot(k1)].
+template <int S>
+__device__ __forceinline__ void pass1(float2 (&v)[16], int t, const float2 *tw256) {
+  dft16<S>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    const float2 w = conj_if(tw256[(t * k1) & 255], S < 0);
+    v[dft16_slot(k1)] = cmul(v[dft16_slot(k1)], w);
+  }
+}
+
+// Pass 1's output of thread t to positions 16 k1 + t of the line, then pass 2: the 16-point DFTs
+// over the rows of the 16 x 16 line matrix. The final value X[t + 16 k2] is multiplied by
+// fin(k2) and written to position t + 16 k2.
+template <int S, bool AB, class Fin>
+__device__ __forceinline__ void pass2(float2 *d, int line, int t, float2 (&v)[16], Fin fin) {
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) d[line_idx<AB>(line, 16 * k1 + t)] = v[dft16_slot(k1)];
+  __syncwarp();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) v[n2] = d[line_idx<AB>(line, 16 * t + n2)];
+  __syncwarp();
+  dft16<S>(v);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) d[line_idx<AB>(line, t + 16 * k2)] = fin(k2, v[dft16_slot(k2)]);
+}
+
+// One transform (sign S) of this CTA's quarter: column transforms (input layout AB or BA), the
+// exchange, row transforms into layout BA. Every thread of every CTA of the cluster calls it.
+template <int S, bool AB>
+__device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, float scale) {
+  const int tid = threadIdx.x;
+  const int t = tid & 15, g = tid >> 4;  // line group: 32 lines at a time
+  float2 *d = sm.d;
+  // column transforms over a, with the four-step twiddle W_N^(S b k) folded into the last write
+#pragma unroll 1
+  for (int line = g; line < kCols; line += kThreads / 16) {
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = d[line_idx<AB>(line, t + 16 * m)];
+    pass1<S>(v, t, sm.tw256);
+    __syncwarp();
+    const float2 lo = conj_if(sm.tlo[line][t], S < 0);
+    pass2<S, AB>(d, line, t, v, [&](int k2, float2 x) {
+      return cmul(x, cmul(lo, conj_if(sm.thi[line][k2], S < 0)));
+    });
+  }
+  cluster.sync();  // every quarter's column transforms are done
+  // pull the values of this CTA's rows k1 = 64 rank + line for b = t + 16 m from their owners
+  constexpr int kRounds = kCols / (kThreads / 16);
+  float2 v[kRounds][16];
+#pragma unroll
+  for (int rd = 0; rd < kRounds; ++rd) {
+    const int k1 = kCols * rank + g + rd * (kThreads / 16);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int b = t + 16 * m;
+      const float2 *src = cluster.map_shared_rank(d, b >> 6);
+      v[rd][m] = src[AB ? ab(k1, b & 63) : ba(b & 63, k1)];
+    }
+    pass1<S>(v[rd], t, sm.tw256);
+  }
+  cluster.sync();  // every pull is done: the quarters may be overwritten
+#pragma unroll
+  for (int rd = 0; rd < kRounds; ++rd) {
+    const int line = g + rd * (kThreads / 16);
+    pass2<S, false>(d, line, t, v[rd], [&](int, float2 x) { return make_float2(x.x * scale, x.y * scale); });
+  }
+  __syncthreads();
+}
+
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 1)
+    fft_cluster_kernel(const __grid_constant__ FftArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  FftSmem &sm = *reinterpret_cast<FftSmem *>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int64_t cl = blockIdx.x / kFftCluster, ncl = gridDim.x / kFftCluster;
+
+  // twiddle tables: W_M^e = (cos(2 pi e / M), -sin(2 pi e / M)), exact integer exponents
+  for (int e = tid; e < 256; e += kThreads) {
+    float sn, cs;
+    sincospif((float)e / 128.f, &sn, &cs);
+    sm.tw256[e] = make_float2(cs, -sn);
+  }
+  for (int i = tid; i < kCols * 16; i += kThreads) {
+    const int j = i >> 4, l = i & 15;
+    const uint32_t b = (uint32_t)(kCols * rank + j);
+    float sn, cs;
+    sincospif((float)((b * (uint32_t)l) & (kN - 1)) / (float)(kN / 2), &sn, &cs);
+    sm.tlo[j][l] = make_float2(cs, -sn);
+    sincospif((float)((b * 16u * (uint32_t)l) & (kN - 1)) / (float)(kN / 2), &sn, &cs);
+    sm.thi[j][l] = make_float2(cs, -sn);
+  }
+  __syncthreads();
+
+  for (int64_t f = cl; f < a.nfft; f += ncl) {
+    // this CTA's columns of row f: element (a, j) = x[256 a + 64 rank + j], layout AB
+    const float2 *src = a.in + f * kN + kCols * rank;
+#pragma unroll 4
+    for (int e = tid; e < kN / 4; e += kThreads) {
+      const int r = e >> 6, j = e & 63;
+      sm.d[ab(r, j)] = __ldcs(src + 256 * r + j);
+    }
+    __syncthreads();
+    for (int s = 0; s < a.nsteps; ++s) {
+      const float scale = a.sign[s] > 0 ? 1.f : 1.f / (float)kN;
+      if (s == 0) {
+        if (a.sign[0] > 0) transform<1, true>(sm, cluster, rank, scale);
+        else transform<-1, true>(sm, cluster, rank, scale);
+      } else {
+        if (a.sign[s] > 0) transform<1, false>(sm, cluster, rank, scale);
+        else transform<-1, false>(sm, cluster, rank, scale);
+      }
+    }
+    // element (j, a) of layout BA is y[256 a + 64 rank + j]
+    float2 *dst = a.out + f * kN + kCols * rank;
+#pragma unroll 4
+    for (int e = tid; e < kN / 4; e += kThreads) {
+      const int r = e >> 6, j = e & 63;
+      __stcs(dst + 256 * r + j, sm.d[ba(j, r)]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t fft_smem_bytes() { return sizeof(FftSmem); }
+
+int fft_max_clusters() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  if (cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(FftSmem)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.gridDim = dim3(kFftCluster);
+  cfg.dynamicSmemBytes = sizeof(FftSmem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void *)fft_cluster_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached = n;
+  return n;
+}
+
+cudaError_t launch_fft(const FftArgs &a, int clusters, cudaStream_t s) {
+  if (a.nsteps < 1 || a.nsteps > kFftMaxSteps || a.nfft < 1 || clusters < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(FftSmem));
+  if (e != cudaSuccess) return e;
+  fft_cluster_kernel<<<dim3(kFftCluster * clusters), dim3(kThreads), sizeof(FftSmem), s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mrw

@@ -305,7 +305,7 @@ bool contains(const mrw_node *root, const mrw_node *x) {
   return false;
 }
 
-bool valid_stage_kind(int k) { return k >= MRW_ST_NOISE_HASH && k <= MRW_ST_SAXPY; }
+bool valid_stage_kind(int k) { return k >= MRW_ST_NOISE_HASH && k <= MRW_ST_IFFT; }
 
 mrw_stage_params default_params(mrw_stage_kind k, const mrw_stage_params *p) {
   mrw_stage_params q{};
@@ -343,7 +343,7 @@ void signature(const mrw_node *n, std::string &s) {
 // ============================================================================================
 // Programs: the tree flattened depth-first (Section 2, single-device execution model)
 // ============================================================================================
-enum Family { F_NONE = 0, F_IMAGE = 1, F_NBODY = 2, F_SAXPY = 3 };
+enum Family { F_NONE = 0, F_IMAGE = 1, F_NBODY = 2, F_SAXPY = 3, F_FFT = 4 };
 
 struct ImgStage {
   int kind;  // OpKind
@@ -368,6 +368,7 @@ struct Program {
   bool has_map = false;
   std::vector<NbStep> nb;
   std::vector<float> alphas;
+  std::vector<int> fft;  // transforms in order: +1 forward, -1 inverse
   int nu = 0, wg = 0;
   // a WHILE_CHANGED loop over img[while_begin, while_end), at most while_max runs (-1: none)
   int while_begin = -1, while_end = -1;
@@ -376,7 +377,7 @@ struct Program {
 
 mrw_status set_family(Program &p, Family f) {
   if (p.fam == F_NONE) p.fam = f;
-  if (p.fam != f) return fail(MRW_ERR_UNSUPPORTED, "a tree mixes image, N-body and saxpy stages");
+  if (p.fam != f) return fail(MRW_ERR_UNSUPPORTED, "a tree mixes image, N-body, saxpy and FFT stages");
   return MRW_OK;
 }
 
@@ -430,6 +431,10 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
       } else if (n->stage == MRW_ST_SAXPY) {
         TRY(set_family(p, F_SAXPY));
         for (int64_t i = 0; i < loop_mult; ++i) p.alphas.push_back(q.alpha);
+      } else if (n->stage == MRW_ST_FFT || n->stage == MRW_ST_IFFT) {
+        TRY(set_family(p, F_FFT));
+        if ((int64_t)p.fft.size() + loop_mult > 4096) return fail(MRW_ERR_UNSUPPORTED, "more than 4096 transforms");
+        for (int64_t i = 0; i < loop_mult; ++i) p.fft.push_back(n->stage == MRW_ST_FFT ? 1 : -1);
       } else {
         return fail(MRW_ERR_INVALID_ARG, "unknown stage kind %d", (int)n->stage);
       }
@@ -479,7 +484,7 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
         return fail(MRW_ERR_UNSUPPORTED, "nested loops with more than one iteration each");
       Program probe;
       TRY(flatten(n->kids[0], probe, depth + 1, false, 1));
-      if (probe.fam == F_IMAGE || probe.fam == F_SAXPY) {
+      if (probe.fam == F_IMAGE || probe.fam == F_SAXPY || probe.fam == F_FFT) {
         // pointwise / stencil bodies: iterations become consecutive stages (fused across iterations)
         for (int64_t i = 0; i < st.max_iters; ++i) TRY(flatten(n->kids[0], p, depth + 1, false, 1));
         return MRW_OK;
@@ -559,7 +564,7 @@ int64_t elem_size(mrw_dtype t) {
     case MRW_U8: return 1;
     case MRW_BF16: return 2;
     case MRW_I32: case MRW_F32: return 4;
-    case MRW_I64: case MRW_F64: return 8;
+    case MRW_I64: case MRW_F64: case MRW_C64: return 8;
   }
   return 0;
 }
@@ -1667,6 +1672,61 @@ mrw_status get_program(const mrw_node *root, Program *p) {
 mrw_status model_predict(mrw_model *m, const float *feat, int *best);
 mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, float *f);
 
+// ============================================================================================
+// FFT trees: rows of kFftN complex values; up to kFftMaxSteps transforms per cluster launch
+// ============================================================================================
+mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *vy) {
+  if (nargs != 2) return fail(MRW_ERR_INVALID_ARG, "FFT trees take x, y");
+  TRY(view_of(args[0], 0, vx));
+  TRY(view_of(args[1], 1, vy));
+  if (args[0].dtype != MRW_C64 || args[1].dtype != MRW_C64)
+    return fail(MRW_ERR_DTYPE, "FFT stages read and write complex float32 (MRW_C64)");
+  if (!same_shape(args[0], args[1])) return fail(MRW_ERR_SHAPE, "x and y differ in shape");
+  if (vx->width != kFftN) return fail(MRW_ERR_SHAPE, "FFT rows hold %d values, not %lld", kFftN, (long long)vx->width);
+  for (int i = 0; i < 2; ++i) {
+    const View &v = i ? *vy : *vx;
+    if (v.pitch != (int64_t)kFftN * 8) return fail(MRW_ERR_SHAPE, "args[%d]: FFT rows must be dense", i);
+    if (v.b->memory == MRW_MEM_DEVICE && (uintptr_t)v.b->data % 8)
+      return fail(MRW_ERR_CONSTRAINT, "args[%d]: complex values need 8-byte alignment", i);
+  }
+  if (args[0].memory == MRW_MEM_DEVICE && args[1].memory == MRW_MEM_DEVICE) {
+    const uintptr_t a0 = (uintptr_t)args[0].data, a1 = a0 + vx->pitch * vx->rows;
+    const uintptr_t b0 = (uintptr_t)args[1].data, b1 = b0 + vy->pitch * vy->rows;
+    if (a0 != b0 && a0 < b1 && b0 < a1) return fail(MRW_ERR_INVALID_ARG, "y overlaps x without being x");
+  }
+  return MRW_OK;
+}
+
+mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg) {
+  View vx, vy;
+  TRY(validate_fft_args(args, nargs, &vx, &vy));
+  const bool inplace = args[0].data == args[1].data;
+  void *dx, *dy;
+  int64_t pp;
+  TRY(resolve(L, vx, true, inplace, &dx, &pp));
+  if (inplace) {
+    dy = dx;
+  } else {
+    TRY(resolve(L, vy, false, true, &dy, &pp));
+  }
+  const int maxc = fft_max_clusters();
+  if (maxc < 1) return fail(MRW_ERR_UNSUPPORTED, "a %d-CTA cluster with %zu bytes of shared memory does not fit",
+                            kFftCluster, fft_smem_bytes());
+  FftArgs a{};
+  a.nfft = vx.rows;
+  const int clusters = (int)std::min<int64_t>(a.nfft, maxc);
+  const int per = cfg.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
+  a.in = (const float2 *)dx;
+  a.out = (float2 *)dy;
+  for (size_t i = 0; i < p.fft.size(); i += per) {
+    a.nsteps = (int32_t)std::min<size_t>(per, p.fft.size() - i);
+    for (int k = 0; k < a.nsteps; ++k) a.sign[k] = p.fft[i + k];
+    CU(launch_fft(a, clusters, L.stream));
+    a.in = (const float2 *)dy;  // later launches continue in place on y
+  }
+  return MRW_OK;
+}
+
 // Argument checks of every family, before any CUDA call.
 mrw_status validate_args(const Program &p, const mrw_buffer *args, int nargs) {
   if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
@@ -1679,6 +1739,7 @@ mrw_status validate_args(const Program &p, const mrw_buffer *args, int nargs) {
     return validate_nbody_args(args, nargs, v);
   }
   View x, y;
+  if (p.fam == F_FFT) return validate_fft_args(args, nargs, &x, &y);
   return validate_saxpy_args(args, nargs, &x, &y);
 }
 
@@ -1718,6 +1779,7 @@ mrw_status enqueue(Launch &L, const Program &p, const mrw_buffer *args, int narg
     case F_IMAGE: TRY(enqueue_image(L, p, args, nargs, cfg, status, used_status)); break;
     case F_NBODY: TRY(enqueue_nbody(L, p, args, nargs, cfg)); break;
     case F_SAXPY: TRY(enqueue_saxpy(L, p, args, nargs, cfg)); break;
+    case F_FFT: TRY(enqueue_fft(L, p, args, nargs, cfg)); break;
     default: return fail(MRW_ERR_INVALID_ARG, "empty tree");
   }
   TRY(copy_back(L));
@@ -2257,6 +2319,18 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
       o << (cta ? "," : "") << "[" << lo << "," << hi - lo << "]";
     }
     o << "]}";
+  } else if (p.fam == F_FFT) {
+    View vx, vy;
+    TRY(validate_fft_args(args, nargs, &vx, &vy));
+    const int per = c.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
+    o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"cluster\":" << kFftCluster
+      << ",\"smem\":" << fft_smem_bytes() << ",\"launches\":[";
+    for (size_t i = 0; i < p.fft.size(); i += per) {
+      o << (i ? "," : "") << "[";
+      for (size_t k = i; k < std::min(p.fft.size(), i + per); ++k) o << (k > i ? "," : "") << (p.fft[k] > 0 ? "\"fft\"" : "\"ifft\"");
+      o << "]";
+    }
+    o << "]}";
   } else {
     o << "{\"family\":\"saxpy\",\"stages\":" << p.alphas.size() << "}";
   }
@@ -2282,7 +2356,8 @@ mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, floa
     nm += s.kind == OP_MIRROR;
     nb += s.kind == OP_BLUR;
   }
-  const double stages = p.fam == F_IMAGE ? (double)p.img.size() : (p.fam == F_SAXPY ? (double)p.alphas.size() : 0.0);
+  const double stages = p.fam == F_IMAGE ? (double)p.img.size()
+                        : (p.fam == F_SAXPY ? (double)p.alphas.size() : (p.fam == F_FFT ? (double)p.fft.size() : 0.0));
   f[4] = (float)stages;
   f[5] = (float)nn;
   f[6] = (float)npw;
@@ -2301,6 +2376,9 @@ mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, floa
   } else if (p.fam == F_SAXPY) {
     bytes = 12.0 * numel;
     ops = 2.0 * stages;
+  } else if (p.fam == F_FFT) {
+    bytes = 16.0 * numel;
+    ops = 5.0 * 16.0 * stages;  // 5 N log2 N flops per transform, per value
   } else {
     bytes = 48.0 * numel;
     ops = 20.0 * numel;

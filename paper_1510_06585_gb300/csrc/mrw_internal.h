@@ -141,6 +141,24 @@ cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t
                           int box_w, int box_h);
 
 // ------------------------------------------------------------------------------------------
+// FFT stages: rows of kFftN complex float32 values, a cluster of kFftCluster CTAs per row
+// ------------------------------------------------------------------------------------------
+constexpr int kFftN = 65536;
+constexpr int kFftCluster = 4;
+constexpr int kFftMaxSteps = 8;
+struct FftArgs {
+  const float2 *in;              // nfft rows of kFftN values (8-byte aligned, dense)
+  float2 *out;                   // same shape; may equal `in`
+  int64_t nfft;
+  int32_t nsteps;                // transforms applied in order, 1..kFftMaxSteps
+  int32_t sign[kFftMaxSteps];    // +1 forward (kernel e^(-2 pi i nk/N)), -1 inverse (e^(+...), / N)
+};
+size_t fft_smem_bytes();
+// Clusters that can be resident at once (0 if the launch configuration is not possible).
+int fft_max_clusters();
+cudaError_t launch_fft(const FftArgs &a, int clusters, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
 // N-body
 // ------------------------------------------------------------------------------------------
 struct LoopCtrl {

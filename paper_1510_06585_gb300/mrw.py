@@ -15,11 +15,11 @@ MRW_OK = 0
 MRW_ERR_INVALID_ARG, MRW_ERR_SHAPE, MRW_ERR_DTYPE, MRW_ERR_CONSTRAINT = 1, 2, 3, 4
 MRW_ERR_OOM, MRW_ERR_CUDA, MRW_ERR_TIMEOUT, MRW_ERR_DEVICE, MRW_ERR_UNSUPPORTED, MRW_ERR_NOT_READY = 5, 6, 7, 8, 9, 10
 
-MRW_U8, MRW_I32, MRW_I64, MRW_F32, MRW_F64, MRW_BF16 = range(6)
+MRW_U8, MRW_I32, MRW_I64, MRW_F32, MRW_F64, MRW_BF16, MRW_C64 = range(7)
 MRW_MEM_DEVICE, MRW_MEM_HOST = 0, 1
 MRW_PARTITION, MRW_COPY = 0, 1
 (MRW_ST_NOISE_HASH, MRW_ST_SOLARISE, MRW_ST_MIRROR_H, MRW_ST_BOXBLUR5, MRW_ST_THRESHOLD3,
- MRW_ST_NBODY_ACCEL, MRW_ST_NBODY_KDK, MRW_ST_SAXPY) = range(8)
+ MRW_ST_NBODY_ACCEL, MRW_ST_NBODY_KDK, MRW_ST_SAXPY, MRW_ST_FFT, MRW_ST_IFFT) = range(10)
 MRW_RED_ADD, MRW_RED_SUB, MRW_RED_MUL, MRW_RED_DIV = range(4)
 MRW_LOOP_FOR, MRW_LOOP_WHILE_CHANGED = 0, 1
 MRW_FUSE_ALL, MRW_FUSE_NONE = 0, 1
@@ -29,7 +29,7 @@ MRW_NOALLOC_MAX_INSTANCES = 256
 
 STAGE_BY_NAME = {"noise": MRW_ST_NOISE_HASH, "solarise": MRW_ST_SOLARISE, "mirror": MRW_ST_MIRROR_H,
                  "blur5": MRW_ST_BOXBLUR5, "threshold3": MRW_ST_THRESHOLD3, "nbody_accel": MRW_ST_NBODY_ACCEL,
-                 "nbody_kdk": MRW_ST_NBODY_KDK, "saxpy": MRW_ST_SAXPY}
+                 "nbody_kdk": MRW_ST_NBODY_KDK, "saxpy": MRW_ST_SAXPY, "fft": MRW_ST_FFT, "ifft": MRW_ST_IFFT}
 
 
 class mrw_buffer(ctypes.Structure):
@@ -169,11 +169,11 @@ def _dtype_code(dt) -> int:
     if isinstance(dt, np.dtype) or isinstance(dt, type):
         d = np.dtype(dt)
         return {np.dtype(np.uint8): MRW_U8, np.dtype(np.int32): MRW_I32, np.dtype(np.int64): MRW_I64,
-                np.dtype(np.float32): MRW_F32, np.dtype(np.float64): MRW_F64}[d]
+                np.dtype(np.float32): MRW_F32, np.dtype(np.float64): MRW_F64, np.dtype(np.complex64): MRW_C64}[d]
     import torch
     if _TORCH_DTYPES is None:
         _TORCH_DTYPES = {torch.uint8: MRW_U8, torch.int32: MRW_I32, torch.int64: MRW_I64, torch.float32: MRW_F32,
-                         torch.float64: MRW_F64, torch.bfloat16: MRW_BF16}
+                         torch.float64: MRW_F64, torch.bfloat16: MRW_BF16, torch.complex64: MRW_C64}
     return _TORCH_DTYPES[dt]
 
 

@@ -1,0 +1,108 @@
+"""GPU parity of the FFT stages (Section 4, FFT pipelined with its inversion) against the FP64
+oracle: rows of 65,536 complex float32 values, one 4-CTA cluster per row.
+
+Tolerance: normwise relative error per row <= 1e-5. A float32 transform of 2^16 points goes
+through 16 radix-2-equivalent levels, each adding a rounding error of a few units of 2^-24 to the
+row's norm, plus one rounded twiddle per value per level group: about 1e-6 in the worst row; a
+wrong twiddle, sign or index anywhere gives an error of order 1."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fft as F
+from paper_1510_06585_gb300 import inputs
+from paper_1510_06585_gb300 import mrw as M
+
+pytestmark = pytest.mark.gpu
+N = 65536
+TOL = 1e-5
+
+
+def tree_of(names):
+    return M.pipeline(*[M.stage(n) for n in names])
+
+
+def run(tree, x, cfg=None, inplace=False, host=False):
+    if host:
+        xd = torch.from_numpy(x.copy())
+        yd = xd if inplace else torch.empty_like(xd)
+    else:
+        xd = torch.from_numpy(x).cuda()
+        yd = xd if inplace else torch.empty_like(xd)
+    M.execute(tree, [xd, yd], cfg).wait(120000)
+    return yd.cpu().numpy()
+
+
+@pytest.mark.parametrize("names", [["fft"], ["ifft"], ["fft", "ifft"], ["ifft", "fft"], ["fft", "fft"]])
+def test_pipelines_match_the_oracle_fused_and_per_stage(names):
+    x = inputs.fft_signals(5, N, seed=len(names) * 7 + (names[0] == "fft"))
+    want = F.pipeline(x, names)
+    for cfg in (M.config(), M.config(fusion=M.MRW_FUSE_NONE)):
+        got = run(tree_of(names), x, cfg)
+        assert F.rel_error(got, want) <= TOL, (names, cfg.fusion, F.rel_error(got, want))
+
+
+def test_closed_forms():
+    x = np.zeros((3, N), np.complex64)
+    x[0, 0] = 1.0                                              # impulse -> all ones
+    k0 = 4321
+    x[1] = np.exp(2j * np.pi * k0 * np.arange(N) / N)          # exponential -> N at k0
+    x[2] = 0.75 - 0.25j                                        # constant -> N (0.75 - 0.25i) at 0
+    X = run(tree_of(["fft"]), x).astype(np.complex128)
+    assert np.abs(X[0] - 1.0).max() <= 1e-6
+    assert abs(X[1, k0] - N) <= 1e-3 * N ** 0.5 and np.abs(np.delete(X[1], k0)).max() <= 1e-3 * N ** 0.5
+    assert abs(X[2, 0] - N * (0.75 - 0.25j)) <= 1e-3 and np.abs(X[2, 1:]).max() <= 1e-3
+
+
+def test_forward_then_inverse_returns_the_input_and_matches_per_stage():
+    x = inputs.fft_signals(7, N, seed=11)
+    tree = tree_of(["fft", "ifft"])
+    fused = run(tree, x)
+    per_stage = run(tree, x, M.config(fusion=M.MRW_FUSE_NONE))
+    assert F.rel_error(fused, x) <= TOL and F.rel_error(per_stage, x) <= TOL
+    assert F.rel_error(fused, per_stage) <= 2 * TOL
+
+
+def test_long_chains_more_rows_than_clusters_in_place_and_host_buffers():
+    # 10 alternating transforms need two fused launches (8 + 2); 83 rows are more than the
+    # clusters resident at once and not a multiple of their number
+    x = inputs.fft_signals(83, N, seed=5)
+    loop = M.loop(tree_of(["fft", "ifft"]), 5)
+    got = run(loop, x)
+    assert F.rel_error(got, x) <= 4 * TOL
+    want = F.fft_rows(x)
+    assert F.rel_error(run(tree_of(["fft"]), x, inplace=True), want) <= TOL
+    assert F.rel_error(run(tree_of(["fft"]), x[:3], host=True), want[:3]) <= TOL
+    assert F.rel_error(run(tree_of(["fft"]), x[:2], host=True, inplace=True), want[:2]) <= TOL
+
+
+def test_one_row_and_plan():
+    x = inputs.fft_signals(1, N, seed=2)[0]  # a 1-D buffer is one row
+    assert F.rel_error(run(tree_of(["ifft"]), x), F.ifft_rows(x)) <= TOL
+    d = M.plan_describe(M.loop(M.stage("fft"), 9), [torch.from_numpy(inputs.fft_signals(2, N)).cuda()] * 2)
+    assert d["family"] == "fft" and [len(l) for l in d["launches"]] == [8, 1] and d["cluster"] == 4
+
+
+def test_rejects_bad_shapes_and_types():
+    bad = torch.zeros(2, 4096, dtype=torch.complex64, device="cuda")
+    with pytest.raises(M.MrwError) as e:
+        M.execute(tree_of(["fft"]), [bad, bad])
+    assert e.value.status == M.MRW_ERR_SHAPE
+    f32 = torch.zeros(2, N, dtype=torch.float32, device="cuda")
+    with pytest.raises(M.MrwError) as e:
+        M.execute(tree_of(["fft"]), [f32, f32])
+    assert e.value.status == M.MRW_ERR_DTYPE
+    with pytest.raises(M.MrwError) as e:
+        M.execute(M.pipeline(M.stage("fft"), M.stage("solarise")), [bad, bad])
+    assert e.value.status == M.MRW_ERR_UNSUPPORTED
+
+
+def test_full_size_256_rows_128_mb():
+    x = inputs.fft_signals(256, N)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    M.execute(tree_of(["fft", "ifft"]), [xd, yd]).wait(120000)
+    assert F.rel_error(yd.cpu().numpy(), x) <= TOL
+    M.execute(tree_of(["fft"]), [xd, yd]).wait(120000)
+    rows = [0, 37, 128, 255]
+    assert F.rel_error(yd.cpu().numpy()[rows], F.fft_rows(x[rows])) <= TOL
