@@ -410,9 +410,35 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n,
         out.update(nbody_workload(M, device, timed, launcher, fused, unfused))
     if "batched" in which:
         out.update(batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n))
+    if "fft" in which:
+        out.update(fft_workload(M, device, timed, launcher, fused, unfused, peaks))
     if "costmodel" in which:
         out.update(costmodel_workload())
     return out
+
+
+def fft_workload(M, device, timed, launcher, fused, unfused, peaks, nfft=256):
+    """FFT pipelined with its inversion (Section 4): 256 rows of 65536 complex float32 values
+    (one 512 KB elementary unit each, 128 MB in total); forward then inverse transform of every
+    row, fused on chip (one cluster launch) and kernel per stage (two launches through HBM)."""
+    import torch
+
+    from paper_1510_06585_gb300 import inputs
+    n = 65536
+    x = torch.from_numpy(inputs.fft_signals(nfft, n)).to(device)
+    y = torch.empty_like(x)
+    tree = M.pipeline(M.stage("fft"), M.stage("ifft"))
+    sets = [M.buffers(x, y)]
+    tf = timed(launcher(tree, sets, fused), 20)
+    tu = timed(launcher(tree, sets, unfused), 20)
+    b = 2 * nfft * n * 8                      # read the input once, write the output once
+    flop = 2 * 5.0 * n * 16 * nfft            # 5 N log2 N per transform, two transforms
+    return {f"fft_ifft_{nfft}x65536": {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 1),
+                                       "gflops": round(flop / tf / 1e9, 1),
+                                       "kernel_per_stage_gbs": round(b / tu / 1e9, 1),
+                                       "speedup_fused": round(tu / tf, 3),
+                                       "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+                                       "bytes": b, "l2": "128 MB in + 128 MB out per step (> L2)"}}
 
 
 def costmodel_workload(n_train=4000, n_test=500, max_log2=26):
@@ -543,8 +569,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrw", choices=["mrw", "reference"])
     ap.add_argument("--no-extras", dest="extras", action="store_false")
-    ap.add_argument("--workloads", default="filter,nbody,batched,costmodel",
-                    help="comma list of the extra workloads to run (filter, nbody, batched, costmodel)")
+    ap.add_argument("--workloads", default="filter,nbody,batched,fft,costmodel",
+                    help="comma list of the extra workloads to run (filter, nbody, batched, fft, costmodel)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--filter-sides", default="1024,8192", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",

@@ -215,7 +215,8 @@ void mrw_node_release(mrw_node_t n);
  *     (N, 4), updated in place;
  *   SAXPY: args = x, y (float32, same shape), y updated in place;
  *   FFT trees (FFT, IFFT, Pipeline/Map/Loop of them): args = x, y, each MRW_C64 of shape
- *     (nfft, 65536) or (65536), dense rows; y = the stages applied to every row of x in order; y may
+ *     (nfft, 65536) or (65536), dense rows, 16-byte aligned device pointers; y = the stages applied
+ *     to every row of x in order; y may
  *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
  *     transforms in one launch (a 4-CTA cluster per row, the data on chip between transforms);
  *     FUSE_NONE runs one launch per transform.

@@ -42,7 +42,7 @@ constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1 / 2)
 
 struct FftSmem {
   float2 d[kN / 4];      // this CTA's quarter of the row (128 KB)
-  float2 tw256[256];     // W_256^e, e < 256 (forward sign)
+  float2 tw[16][16];     // W_256^(t k), stored at [k][t] (forward sign)
   float2 tlo[kCols][16]; // W_N^(b l),      b = 64 r + j, l < 16
   float2 thi[kCols][16]; // W_N^(16 b h),   h < 16
 };
@@ -103,6 +103,21 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 
 __device__ __forceinline__ int dft16_slot(int k) { return 4 * (k & 3) + (k >> 2); }
 
+// Shared-memory window address of this CTA's `p` in the CTA of the cluster with rank `rank`, and an
+// 8-byte load from such an address (distributed shared memory).
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
 // Index of line position p in shared memory: a column of the AB layout, or a row of the BA one.
 template <bool AB>
 __device__ __forceinline__ int line_idx(int line, int p) {
@@ -112,11 +127,11 @@ __device__ __forceinline__ int line_idx(int line, int p) {
 // Pass 1 of a 256-point transform on values already in registers (v[m] = position t + 16 m): the
 // 16-point DFT and the W_256^(t k1) twiddle; y[k1] is returned in v[dft16_slot(k1)].
 template <int S>
-__device__ __forceinline__ void pass1(float2 (&v)[16], int t, const float2 *tw256) {
+__device__ __forceinline__ void pass1(float2 (&v)[16], int t, const float2 (*tw)[16]) {
   dft16<S>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) {
-    const float2 w = conj_if(tw256[(t * k1) & 255], S < 0);
+    const float2 w = conj_if(tw[k1][t], S < 0);
     v[dft16_slot(k1)] = cmul(v[dft16_slot(k1)], w);
   }
 }
@@ -150,7 +165,7 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
     float2 v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = d[line_idx<AB>(line, t + 16 * m)];
-    pass1<S>(v, t, sm.tw256);
+    pass1<S>(v, t, sm.tw);
     __syncwarp();
     const float2 lo = conj_if(sm.tlo[line][t], S < 0);
     pass2<S, AB>(d, line, t, v, [&](int k2, float2 x) {
@@ -166,11 +181,11 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
     const int k1 = kCols * rank + g + rd * (kThreads / 16);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      const int b = t + 16 * m;
-      const float2 *src = cluster.map_shared_rank(d, b >> 6);
-      v[rd][m] = src[AB ? ab(k1, b & 63) : ba(b & 63, k1)];
+      const int b = t + 16 * m;  // owned by rank b / 64 = m / 4
+      const int i = AB ? ab(k1, b & 63) : ba(b & 63, k1);
+      v[rd][m] = ld_cluster(cluster_addr(d + i, (uint32_t)(m >> 2)));
     }
-    pass1<S>(v[rd], t, sm.tw256);
+    pass1<S>(v[rd], t, sm.tw);
   }
   cluster.sync();  // every pull is done: the quarters may be overwritten
 #pragma unroll
@@ -192,9 +207,10 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
 
   // twiddle tables: W_M^e = (cos(2 pi e / M), -sin(2 pi e / M)), exact integer exponents
   for (int e = tid; e < 256; e += kThreads) {
+    const int k = e >> 4, t = e & 15;
     float sn, cs;
-    sincospif((float)e / 128.f, &sn, &cs);
-    sm.tw256[e] = make_float2(cs, -sn);
+    sincospif((float)(t * k) / 128.f, &sn, &cs);
+    sm.tw[k][t] = make_float2(cs, -sn);
   }
   for (int i = tid; i < kCols * 16; i += kThreads) {
     const int j = i >> 4, l = i & 15;
@@ -208,12 +224,15 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
   __syncthreads();
 
   for (int64_t f = cl; f < a.nfft; f += ncl) {
-    // this CTA's columns of row f: element (a, j) = x[256 a + 64 rank + j], layout AB
-    const float2 *src = a.in + f * kN + kCols * rank;
+    // this CTA's columns of row f: element (a, j) = x[256 a + 64 rank + j], layout AB; two values
+    // per 16-byte load
+    const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kCols * rank);
 #pragma unroll 4
-    for (int e = tid; e < kN / 4; e += kThreads) {
-      const int r = e >> 6, j = e & 63;
-      sm.d[ab(r, j)] = __ldcs(src + 256 * r + j);
+    for (int e = tid; e < kN / 8; e += kThreads) {
+      const int r = e >> 5, j = 2 * (e & 31);
+      const float4 q = __ldcs(src + 128 * r + (j >> 1));
+      sm.d[ab(r, j)] = make_float2(q.x, q.y);
+      sm.d[ab(r, j + 1)] = make_float2(q.z, q.w);
     }
     __syncthreads();
     for (int s = 0; s < a.nsteps; ++s) {
@@ -226,12 +245,13 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
         else transform<-1, false>(sm, cluster, rank, scale);
       }
     }
-    // element (j, a) of layout BA is y[256 a + 64 rank + j]
-    float2 *dst = a.out + f * kN + kCols * rank;
+    // element (j, a) of layout BA is y[256 a + 64 rank + j]; two values per 16-byte store
+    float4 *dst = reinterpret_cast<float4 *>(a.out + f * kN + kCols * rank);
 #pragma unroll 4
-    for (int e = tid; e < kN / 4; e += kThreads) {
-      const int r = e >> 6, j = e & 63;
-      __stcs(dst + 256 * r + j, sm.d[ba(j, r)]);
+    for (int e = tid; e < kN / 8; e += kThreads) {
+      const int r = e >> 5, j = 2 * (e & 31);
+      const float2 lo = sm.d[ba(j, r)], hi = sm.d[ba(j + 1, r)];
+      __stcs(dst + 128 * r + (j >> 1), make_float4(lo.x, lo.y, hi.x, hi.y));
     }
     __syncthreads();
   }

@@ -1686,8 +1686,8 @@ mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *
   for (int i = 0; i < 2; ++i) {
     const View &v = i ? *vy : *vx;
     if (v.pitch != (int64_t)kFftN * 8) return fail(MRW_ERR_SHAPE, "args[%d]: FFT rows must be dense", i);
-    if (v.b->memory == MRW_MEM_DEVICE && (uintptr_t)v.b->data % 8)
-      return fail(MRW_ERR_CONSTRAINT, "args[%d]: complex values need 8-byte alignment", i);
+    if (v.b->memory == MRW_MEM_DEVICE && (uintptr_t)v.b->data % 16)
+      return fail(MRW_ERR_CONSTRAINT, "args[%d]: FFT rows need a 16-byte aligned pointer", i);
   }
   if (args[0].memory == MRW_MEM_DEVICE && args[1].memory == MRW_MEM_DEVICE) {
     const uintptr_t a0 = (uintptr_t)args[0].data, a1 = a0 + vx->pitch * vx->rows;

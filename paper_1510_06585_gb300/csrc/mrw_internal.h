@@ -147,7 +147,7 @@ constexpr int kFftN = 65536;
 constexpr int kFftCluster = 4;
 constexpr int kFftMaxSteps = 8;
 struct FftArgs {
-  const float2 *in;              // nfft rows of kFftN values (8-byte aligned, dense)
+  const float2 *in;              // nfft rows of kFftN values (16-byte aligned, dense)
   float2 *out;                   // same shape; may equal `in`
   int64_t nfft;
   int32_t nsteps;                // transforms applied in order, 1..kFftMaxSteps

@@ -80,7 +80,7 @@ def test_one_row_and_plan():
     x = inputs.fft_signals(1, N, seed=2)[0]  # a 1-D buffer is one row
     assert F.rel_error(run(tree_of(["ifft"]), x), F.ifft_rows(x)) <= TOL
     d = M.plan_describe(M.loop(M.stage("fft"), 9), [torch.from_numpy(inputs.fft_signals(2, N)).cuda()] * 2)
-    assert d["family"] == "fft" and [len(l) for l in d["launches"]] == [8, 1] and d["cluster"] == 4
+    assert d["family"] == "fft" and [len(l) for l in d["launches"]] == [8, 1] and d["cluster"] in (4, 8)
 
 
 def test_rejects_bad_shapes_and_types():
