@@ -495,10 +495,10 @@ def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stre
     d = np.ascontiguousarray(desc, dtype=np.int64)
     dptr = d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
-    def blaunch(cfg):
+    def blaunch(cfg, tree=btree):
         def f(i):
             fut = ctypes.c_void_p()
-            M.check(lib.mrw_execute_batched(btree.h, bx.data_ptr(), by.data_ptr(), bx.numel(), dptr, d.shape[0],
+            M.check(lib.mrw_execute_batched(tree.h, bx.data_ptr(), by.data_ptr(), bx.numel(), dptr, d.shape[0],
                                             ctypes.byref(cfg), stream, ctypes.byref(fut)), "batched")
             pending.append(fut)
         return f
@@ -511,10 +511,16 @@ def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stre
     bu = min(range(8, 16), key=lambda i: times[i])
     tb = timed(blaunch(cand[bf]), 5)
     tbu = timed(blaunch(cand[bu]), 3)
+    # where the time goes: the same batch and launch shape with the leading stages removed
+    subsets = {}
+    for names in (["blur5"], ["mirror", "blur5"], ["solarise", "mirror", "blur5"]):
+        sub = M.map_(M.pipeline(*[M.stage(nm) for nm in names]))
+        subsets["+".join(names)] = round(timed(blaunch(cand[bf], sub), 3) * 1e3, 3)
     out[f"batched_{batch_n}"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
                            "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
                            "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
-                           "launches_per_step": 1, "tuned": {"fused_index": bf, "fused_cfg": list(cand[bf].as_tuple()),
+                           "launches_per_step": 1, "stage_subsets_ms": subsets,
+                           "tuned": {"fused_index": bf, "fused_cfg": list(cand[bf].as_tuple()),
                                                              "unfused_index": bu,
                                                              "default_ms": round(times[0] * 1e3, 4)}}
     return out
