@@ -196,6 +196,16 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
   __syncthreads();
 }
 
+// Row r and first column j of the 16-byte unit e (0 .. 8191) of a CTA's part, for the global loads
+// and stores: a warp covers two rows (r even and r + 1) and half of their 64 columns, 8 lanes per
+// 128-byte segment; each half warp then touches 16 distinct bank pairs in both layouts (the
+// swizzles of rows r and r + 1 differ in their lowest bit).
+__device__ __forceinline__ void fft_io_slot(int e, int *r, int *j) {
+  const int ws = e >> 5, lane = e & 31;
+  *r = 2 * (ws >> 1) + ((lane >> 3) & 1);
+  *j = 32 * (ws & 1) + 2 * ((lane & 7) + 8 * (lane >> 4));
+}
+
 __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 1)
     fft_cluster_kernel(const __grid_constant__ FftArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -229,7 +239,8 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kCols * rank);
 #pragma unroll 4
     for (int e = tid; e < kN / 8; e += kThreads) {
-      const int r = e >> 5, j = 2 * (e & 31);
+      int r, j;
+      fft_io_slot(e, &r, &j);
       const float4 q = __ldcs(src + 128 * r + (j >> 1));
       sm.d[ab(r, j)] = make_float2(q.x, q.y);
       sm.d[ab(r, j + 1)] = make_float2(q.z, q.w);
@@ -249,7 +260,8 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     float4 *dst = reinterpret_cast<float4 *>(a.out + f * kN + kCols * rank);
 #pragma unroll 4
     for (int e = tid; e < kN / 8; e += kThreads) {
-      const int r = e >> 5, j = 2 * (e & 31);
+      int r, j;
+      fft_io_slot(e, &r, &j);
       const float2 lo = sm.d[ba(j, r)], hi = sm.d[ba(j + 1, r)];
       __stcs(dst + 128 * r + (j >> 1), make_float4(lo.x, lo.y, hi.x, hi.y));
     }
