@@ -724,8 +724,10 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
             ta += h02[j];
             tb += h13[j];
             const uint32_t v02 = suf02[j] + ta, v13 = suf13[j] + tb;
-            // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane: high lane mulhi(v, 5243) >> 1,
-            // low lane the same on v << 16 (exact over the whole range of both lanes)
+            // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane, as a multiplication (division by
+            // an invariant integer, Granlund and Montgomery 1994): high lane mulhi(v, 5243) >> 1,
+            // low lane the same on v << 16; 5243 = ceil(2^17 / 25), exact over the whole range of
+            // both lanes whatever the other lane holds (checked exhaustively)
             const uint32_t d0 = __umulhi(v02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(v02, 5243u) >> 1;
             const uint32_t d1 = __umulhi(v13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(v13, 5243u) >> 1;
             o[j] = d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u;

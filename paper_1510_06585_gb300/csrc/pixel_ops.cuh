@@ -51,11 +51,25 @@ __device__ __forceinline__ uint32_t thresh4(uint32_t a, uint32_t t0, uint32_t t1
   return (ge4(a, t0, t0 & kLo7) >> 7) + (ge4(a, t1, t1 & kLo7) >> 7);
 }
 
+// (z ^ (z >> 16)) mod 41: the finaliser's last xor-shift and the modulo together. With zh = z >> 16
+// the value is zh 2^16 + ((z ^ zh) & 0xFFFF) and 2^16 = 18 (mod 41), so it is congruent to
+// s = 18 zh + ((z ^ zh) & 0xFFFF) < 2^21. The quotient s / 41 is mulhi(s, 104755328), where
+// 104755328 = 32 ceil(2^27 / 41): division by an invariant integer as a multiplication
+// (Granlund and Montgomery, 1994), exact for every s below 2^21 (checked exhaustively). Only the
+// shift and the xor use the integer ALU pipe; the rest runs on the multiply pipe.
+__device__ __forceinline__ uint32_t mix_tail_mod41(uint32_t z) {
+  const uint32_t zh = z >> 16;
+  const uint32_t s = 18u * zh + ((z ^ zh) & 0xFFFFu);
+  return s - 41u * __umulhi(s, 104755328u);
+}
+
 // One pixel of the noise stage, written as max(min(p + r, 275) - 20, 0) with r = h mod 41:
 // each bound is one add-and-compare instruction.
 __device__ __forceinline__ uint32_t noise_px(uint32_t p, uint32_t colpre, uint32_t ypre) {
-  const uint32_t h = fmix32_tail(colpre ^ ypre);
-  const uint32_t r = h % 41u;
+  uint32_t h = (colpre ^ ypre) * 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  const uint32_t r = mix_tail_mod41(h);
   return (uint32_t)__viaddmax_s32(__viaddmin_s32((int)p, (int)r, 275), -20, 0);
 }
 
