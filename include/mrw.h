@@ -68,7 +68,10 @@ typedef enum mrw_dtype { MRW_U8 = 0, MRW_I32 = 1, MRW_I64 = 2, MRW_F32 = 3, MRW_
 
 /* Where `data` lives. HOST buffers (pageable or pinned) are staged through device memory the
  * executor allocates per call and frees when the call's work is done, the way the paper's
- * Vector container hides data location and transfers (Section 2.1). */
+ * Vector container hides data location and transfers (Section 2.1). Exception: when a whole image
+ * tree fuses into one pointwise kernel and both image buffers are page-locked host memory mapped
+ * into the device address space (e.g. cudaHostAlloc / torch pin_memory) with 16-byte aligned rows,
+ * the kernel reads and writes them in place over the host link. */
 typedef enum mrw_memory { MRW_MEM_DEVICE = 0, MRW_MEM_HOST = 1 } mrw_memory;
 
 /* Transfer mode (Section 3.4): PARTITION splits the vector among the parallel executions by its

@@ -666,6 +666,20 @@ mrw_status resolve(Launch &L, const View &v, bool copy_in, bool copy_out, void *
   return MRW_OK;
 }
 
+// Device address of a page-locked host buffer mapped into the device address space, if the buffer
+// is one and its rows suit the streaming kernels (16-byte aligned start and pitch).
+bool mapped_host(const View &v, void **dev) {
+  if (v.b->memory != MRW_MEM_HOST || (uintptr_t)v.b->data % 16 || v.pitch % 16) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, v.b->data) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+  *dev = at.devicePointer;
+  return true;
+}
+
 mrw_status copy_back(Launch &L) {
   for (const Staged &s : L.staged)
     if (s.copy_back)
@@ -1424,13 +1438,19 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
   const ImgGeom geo = geom_of(args[0], vin);
   if (p.while_begin >= 0) return enqueue_image_while(L, p, vin, vout, geo, cfg, status, used_status);
   const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
-  if (L.events && gs.size() == 1 && !gs[0].use_stencil && vin.b->memory == MRW_MEM_HOST &&
-      vout.b->memory == MRW_MEM_HOST && geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20))
-    return enqueue_image_overlapped(L, gs[0], vin, vout, p.reduce != RED_NONE ? &vred : nullptr, geo, cfg, p.wg);
-  void *din, *dout;
-  int64_t pin, pout;
-  TRY(resolve(L, vin, true, false, &din, &pin));
-  TRY(resolve(L, vout, false, true, &dout, &pout));
+  const bool one_chain = gs.size() == 1 && !gs[0].use_stencil && vin.b->memory == MRW_MEM_HOST &&
+                         vout.b->memory == MRW_MEM_HOST;
+  void *din = nullptr, *dout = nullptr;
+  int64_t pin = vin.pitch, pout = vout.pitch;
+  // Page-locked host buffers mapped into the device address space, read once and written once by
+  // a single streaming kernel: the kernel reads and writes them in place over the host link
+  // (NVLink-C2C on Grace-Blackwell), which moves the bytes faster than staging copies do.
+  if (!(one_chain && mapped_host(vin, &din) && mapped_host(vout, &dout))) {
+    if (one_chain && L.events && geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20))
+      return enqueue_image_overlapped(L, gs[0], vin, vout, p.reduce != RED_NONE ? &vred : nullptr, geo, cfg, p.wg);
+    TRY(resolve(L, vin, true, false, &din, &pin));
+    TRY(resolve(L, vout, false, true, &dout, &pout));
+  }
   unsigned long long *red = nullptr;
   void *dred = nullptr;
   int64_t pred = 0;

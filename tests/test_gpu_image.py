@@ -159,6 +159,29 @@ def test_future_elapsed_and_query():
     assert e.value.status == M.MRW_ERR_INVALID_ARG
 
 
+def test_pinned_host_buffers_are_read_and_written_in_place():
+    # page-locked host buffers with 16-byte rows: the single fused kernel reads and writes them in
+    # place over the host link; counts, the noise hash's global rows and a pageable output (staged
+    # path) must all give the oracle's bytes
+    vol = inputs.volume(24, 256, 512, seed=21)
+    pin_in = torch.from_numpy(vol).pin_memory()
+    pin_out = torch.zeros_like(pin_in).pin_memory()
+    counts = torch.full((3,), -1, dtype=torch.int64).pin_memory()
+    seg = M.mapreduce(M.map_(M.stage("threshold3")))
+    for _ in range(2):
+        M.execute(seg, [pin_in, pin_out, counts]).wait(120000)
+        labels_w, counts_w = O.segmentation(vol)
+        assert np.array_equal(pin_out.numpy(), labels_w) and np.array_equal(counts.numpy(), counts_w)
+    img = inputs.filter_image(1024, 2048, seed=3)
+    pi = torch.from_numpy(img).pin_memory()
+    po = torch.zeros_like(pi).pin_memory()
+    M.execute(build_image_tree(FILTER, {0: 2}), [pi, po]).wait(120000)
+    assert np.array_equal(po.numpy(), O.filter_pipeline(img, 2))
+    pageable = np.zeros_like(img)
+    M.execute(build_image_tree(FILTER, {0: 2}), [pi, pageable]).wait(120000)
+    assert np.array_equal(pageable, O.filter_pipeline(img, 2))
+
+
 def test_large_host_buffers_take_the_overlapped_chunked_path():
     # above 8 MiB the host rows are staged in chunks whose copies overlap the kernels; each chunk's
     # noise hash uses its global row (Offset trait) and the counts accumulate across chunks
