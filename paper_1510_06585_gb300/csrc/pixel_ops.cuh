@@ -63,24 +63,25 @@ __device__ __forceinline__ uint32_t mix_tail_mod41(uint32_t z) {
   return s - 41u * __umulhi(s, 104755328u);
 }
 
-// One pixel of the noise stage, written as max(min(p + r, 275) - 20, 0) with r = h mod 41:
-// each bound is one add-and-compare instruction.
-__device__ __forceinline__ uint32_t noise_px(uint32_t p, uint32_t colpre, uint32_t ypre) {
+// h mod 41 of one pixel's hash h = F(colpre ^ ypre).
+__device__ __forceinline__ uint32_t noise_r(uint32_t colpre, uint32_t ypre) {
   uint32_t h = (colpre ^ ypre) * 0x85EBCA6Bu;
   h ^= h >> 13;
   h *= 0xC2B2AE35u;
-  const uint32_t r = mix_tail_mod41(h);
-  return (uint32_t)__viaddmax_s32(__viaddmin_s32((int)p, (int)r, 275), -20, 0);
+  return mix_tail_mod41(h);
 }
 
-// The noise stage on the 4 pixels of a word; c[k] is pixel k's colpre.
+// The noise stage on the 4 pixels of a word (pixel k's colpre in ck), as
+// max(min(p + r, 275) - 20, 0): pixels 0, 2 and 1, 3 go through the clamp two at a time in
+// 16-bit lanes (an add-and-compare instruction per bound and pair).
 __device__ __forceinline__ uint32_t noise4(uint32_t q, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                            uint32_t ypre) {
-  const uint32_t r0 = noise_px(q & 0xFFu, c0, ypre);
-  const uint32_t r1 = noise_px(__byte_perm(q, 0, 0x4441), c1, ypre);
-  const uint32_t r2 = noise_px(__byte_perm(q, 0, 0x4442), c2, ypre);
-  const uint32_t r3 = noise_px(q >> 24, c3, ypre);
-  return r0 + r1 * 0x100u + r2 * 0x10000u + r3 * 0x1000000u;  // bytes: the adds do not carry
+  const uint32_t r02 = noise_r(c0, ypre) + noise_r(c2, ypre) * 0x10000u;
+  const uint32_t r13 = noise_r(c1, ypre) + noise_r(c3, ypre) * 0x10000u;
+  const uint32_t p02 = __byte_perm(q, 0, 0x4240), p13 = __byte_perm(q, 0, 0x4341);
+  const uint32_t t02 = __viaddmax_s16x2(__viaddmin_s16x2(p02, r02, 0x01130113u), 0xFFECFFECu, 0u);
+  const uint32_t t13 = __viaddmax_s16x2(__viaddmin_s16x2(p13, r13, 0x01130113u), 0xFFECFFECu, 0u);
+  return t02 + t13 * 0x100u;  // bytes 0, 2 and 1, 3: the add does not carry
 }
 
 __device__ __forceinline__ uint32_t noise4(uint32_t q, const uint32_t (&c)[4], uint32_t ypre) {
