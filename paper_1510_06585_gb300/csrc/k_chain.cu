@@ -32,17 +32,23 @@ __device__ __forceinline__ uint4 ld16(const uint8_t *p) {
 // 16 source bytes of output segment [xo, xo+16) for a mirrored chain: output byte k comes from
 // source column W-1-xo-k. The source window [s, s+16), s = W-xo-16, starts r = W mod 16 bytes
 // past the aligned address a0 = s - r (a0 may be -16 for the row's tail segment, whose first
-// aligned vector is then not read).
-__device__ __forceinline__ uint4 load_mirrored(const uint8_t *row, int xo, int W, int q0, uint32_t sel) {
-  const int s = W - xo - 16;
-  const int a0 = s - (W & 15);
+// aligned vector is then not read). The loads (mirrored_issue) and the byte permutation
+// (mirrored_finish) are split so that a row's loads can be in flight while the previous rows are
+// computed.
+__device__ __forceinline__ void mirrored_issue(const uint8_t *row, int xo, int W, uint4 &lo, uint4 &hi) {
+  const int a0 = W - xo - 16 - (W & 15);
   if ((W & 15) == 0) {
-    const uint4 v = ld16(row + a0);
-    return make_uint4(__byte_perm(v.w, 0, 0x0123), __byte_perm(v.z, 0, 0x0123), __byte_perm(v.y, 0, 0x0123),
-                      __byte_perm(v.x, 0, 0x0123));
+    hi = ld16(row + a0);
+  } else {
+    lo = a0 >= 0 ? ld16(row + a0) : make_uint4(0, 0, 0, 0);
+    hi = ld16(row + a0 + 16);
   }
-  const uint4 lo = a0 >= 0 ? ld16(row + a0) : make_uint4(0, 0, 0, 0);
-  const uint4 hi = ld16(row + a0 + 16);
+}
+
+__device__ __forceinline__ uint4 mirrored_finish(const uint4 &lo, const uint4 &hi, int W, int q0, uint32_t sel) {
+  if ((W & 15) == 0)
+    return make_uint4(__byte_perm(hi.w, 0, 0x0123), __byte_perm(hi.z, 0, 0x0123), __byte_perm(hi.y, 0, 0x0123),
+                      __byte_perm(hi.x, 0, 0x0123));
   uint32_t w0, w1, w2, w3, w4;
   switch (q0) {
     case 0: w0 = lo.x; w1 = lo.y; w2 = lo.z; w3 = lo.w; w4 = hi.x; break;
@@ -113,11 +119,11 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4]
 __device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01010101u, 0u); }
 
 // CTAs per SM the registers of a variant are budgeted for (at most 64 registers for 4, 80 for 3,
-// 128 for 2). Chains with noise keep 16 column hashes per noise op in registers and are ALU-bound,
-// so their budget follows the unroll depth; chains without noise keep the compiler's own choice
-// (0: no minimum; 60 registers at unroll 4).
+// 128 for 2). Chains with noise keep 16 column hashes per noise op and the next rows' loads in
+// registers and are ALU-bound, so their budget follows the unroll depth; chains without noise
+// keep the compiler's own choice (0: no minimum).
 constexpr int chain_min_blocks(int nn, int u) {
-  return nn == 0 ? 0 : (nn == 1 ? (u <= 2 ? 4 : (u == 4 ? 3 : 2)) : (u <= 2 ? 2 : 1));
+  return nn == 0 ? 0 : (nn == 1 ? (u == 1 ? 4 : (u == 2 ? 3 : (u == 4 ? 2 : 1))) : (u <= 2 ? 2 : 1));
 }
 
 template <int NN, bool MIR, int U>
@@ -189,15 +195,43 @@ __global__ void __launch_bounds__(256, chain_min_blocks(NN, U)) chain_kernel(con
     // persistent order: rows r0 + (k U + u) step; blocked order: rows (r0 + k step) U + u
     const int64_t step = a.rows_parallel;
     const int64_t ustep = a.blocked ? 1 : step;
-    for (int64_t y0 = a.blocked ? (int64_t)r0 * U : (int64_t)r0; y0 < a.rows; y0 += U * step) {
+    // Chains with noise stages are software-pipelined: the loads of the next U rows are issued
+    // before the current U rows are computed, so each warp has a full iteration of hash arithmetic
+    // to cover their latency. Chains without noise are HBM-bound and spend their registers on
+    // occupancy instead: they load each iteration's rows at its start.
+    constexpr bool kAhead = NN > 0;
+    uint4 plo[U], phi[U];
+    auto issue = [&](int64_t ys) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t y = ys + u * ustep;
+        plo[u] = phi[u] = make_uint4(0, 0, 0, 0);
+        if (y < a.rows) {
+          const uint8_t *row = a.in + y * a.in_pitch;
+          if constexpr (MIR) mirrored_issue(row, xo, W, plo[u], phi[u]);
+          else phi[u] = ld16(row + xo);
+        }
+      }
+    };
+    int64_t y0 = a.blocked ? (int64_t)r0 * U : (int64_t)r0;
+    if (kAhead && y0 < a.rows) issue(y0);
+    for (; y0 < a.rows; y0 += U * step) {
       uint32_t w[U][4], ypre[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t y = y0 + u * ustep;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (y < a.rows) {
+        if constexpr (kAhead) {
+          v = MIR ? mirrored_finish(plo[u], phi[u], W, q0, sel) : phi[u];
+        } else if (y < a.rows) {
           const uint8_t *row = a.in + y * a.in_pitch;
-          v = MIR ? load_mirrored(row, xo, W, q0, sel) : ld16(row + xo);
+          if constexpr (MIR) {
+            uint4 lo = make_uint4(0, 0, 0, 0), hi;
+            mirrored_issue(row, xo, W, lo, hi);
+            v = mirrored_finish(lo, hi, W, q0, sel);
+          } else {
+            v = ld16(row + xo);
+          }
         }
         w[u][0] = v.x;
         w[u][1] = v.y;
@@ -206,6 +240,7 @@ __global__ void __launch_bounds__(256, chain_min_blocks(NN, U)) chain_kernel(con
         const uint32_t y32 = (uint32_t)(y + a.row0);
         ypre[u] = y32 ^ (y32 >> 16);
       }
+      if (kAhead && y0 + U * step < a.rows) issue(y0 + U * step);
       if constexpr (NN == 0) {
         apply_chain<0, U>(a, w, ch, ypre);
       } else {
