@@ -33,9 +33,17 @@ __device__ __forceinline__ uint32_t fmix32_tail(uint32_t h) {
   return h;
 }
 
+// Byte k of the result is 0xFF if byte k of w has its top bit set, else 0: prmt's default mode
+// with the sign-replicate bit set in every selector nibble (selectors 8 + k).
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t w) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(d) : "r"(w));
+  return d;
+}
+
 __device__ __forceinline__ uint32_t solarise4(uint32_t w) {
   // p >= 128 -> 255 - p == p ^ 0xFF; the top bit of each byte selects the flip
-  return w ^ (((w >> 7) & 0x01010101u) * 0xFFu);
+  return w ^ sign_bytes(w);
 }
 
 // Per byte: 0x80 if a >= t, else 0. Setting a's top bits and clearing t's makes the subtraction
