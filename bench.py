@@ -359,7 +359,7 @@ def tune_candidates_buffers(M, tree, bufarr, reps=5):
                                 "default_ms": round(float(t[0]), 5), "best_ms": round(float(t[bf]), 5)}
 
 
-def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n, filter_sides="1024,8192"):
+def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n, filter_sides="1024,4096,8192,16384"):
     import torch
 
     from paper_1510_06585_gb300 import inputs
@@ -391,7 +391,9 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n,
     # Filter Pipeline (noise -> solarise -> mirror)
     ftree = M.pipeline(M.stage("noise", seed=2), M.stage("solarise"), M.stage("mirror"))
     sides = [int(v) for v in filter_sides.split(",") if v] if "filter" in which else []
-    for side, nsets in ((v, 1 if v <= 2048 else 2) for v in sides):
+    # sides up to 2048 are L2-resident (reported as latency); above, enough rotating input/output
+    # sets that consecutive steps touch at least 512 MiB (about 4x L2), at least two sets
+    for side, nsets in ((v, 1 if v <= 2048 else max(2, -(-(512 << 20) // (2 * v * v)))) for v in sides):
         img = inputs.filter_image(side, side)
         sets = []
         for _ in range(nsets):
@@ -405,7 +407,8 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n,
         out[f"filter_{side}"] = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2), "tuned": tinfo,
                                  "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
                                  "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
-                                 "l2": "resident (2 MiB)" if side == 1024 else "2 rotating sets, 256 MiB"}
+                                 "l2": (f"resident ({b >> 20} MiB)" if nsets == 1 and side <= 2048 else
+                                        f"{nsets} rotating sets, {nsets * b >> 20} MiB")}
     if "nbody" in which:
         out.update(nbody_workload(M, device, timed, launcher, fused, unfused))
     if "batched" in which:
@@ -578,7 +581,7 @@ def main():
     ap.add_argument("--workloads", default="filter,nbody,batched,fft,costmodel",
                     help="comma list of the extra workloads to run (filter, nbody, batched, fft, costmodel)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
-    ap.add_argument("--filter-sides", default="1024,8192", help="image sides of the Filter Pipeline workload")
+    ap.add_argument("--filter-sides", default="1024,4096,8192,16384", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
                     help="skip the headline timing (profiling runs of one extra workload)")
     args = ap.parse_args()
