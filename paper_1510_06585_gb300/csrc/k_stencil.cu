@@ -430,21 +430,21 @@ struct RowItem {
   uint32_t seed_xor;
 };
 
-// Issue-side state of a warp (lane 0 writes it, every lane may read it).
+// Issue-side state of a warp: every lane holds the same copy in registers (the lanes run the
+// issue path together; lane 0 alone writes shared memory and starts the copies).
 struct RowIssue {
-  int32_t item;   // FIFO slot of the item being issued (-1: none)
-  int32_t j;      // next chunk of that item
-  int32_t count;  // chunks issued so far
-  int32_t tail;   // FIFO slots written so far
-  int32_t done;   // the tile counter is exhausted
-  int32_t pad[3];
+  int32_t item;     // FIFO slot of the item being issued (-1: none)
+  int32_t j;        // next chunk of that item
+  int32_t nchunks;  // chunks of that item
+  int32_t count;    // chunks issued so far
+  int32_t tail;     // FIFO slots written so far
+  int32_t done;     // the tile counter is exhausted
 };
 
 struct alignas(128) RowWarpSmem {
   uint8_t buf[kRowsBufs][kRowsChunk][kRowsBoxW];
   uint64_t bar[kRowsBufs];
   RowItem fifo[kRowsFifo];
-  RowIssue iss;
 };
 
 // Index of the last instance whose first tile is <= t (all lanes; ninst >= 1). Each round the 32
@@ -464,53 +464,60 @@ __device__ __forceinline__ int warp_find_instance(const int64_t *prefix, int nin
   return lo;
 }
 
-// Claim one more chunk into the ring (all lanes call it; lane 0 writes and issues).
+// Claims the next work item from the tile counter and decodes it into the next FIFO slot (all
+// lanes call it; lane 0 writes the slot).
 template <bool MIR>
-__device__ __noinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, int lane) {
-  RowIssue st = w.iss;
-  if (st.done) return;
-  if (st.item < 0 || st.j == w.fifo[st.item % kRowsFifo].nchunks) {
-    unsigned int t = 0;
-    if (lane == 0) t = atomicAdd(a.queue, 1u);
-    t = __shfl_sync(0xFFFFFFFFu, t, 0);
-    RowItem it;
-    if ((int64_t)t >= a.total_tiles) {
-      it.inst = -1;
-      st.done = 1;
-    } else {
-      const int i = warp_find_instance(a.tile_prefix, a.ninst, (int64_t)t, lane);
-      const StencilInstance in = a.inst[i];
-      const int64_t lt = (int64_t)t - a.tile_prefix[i];
-      const int64_t per_plane = (int64_t)in.tiles_x * in.tiles_y;
-      const int z = (int)(lt / per_plane);
-      const int rem = (int)(lt - (int64_t)z * per_plane);
-      const int seg = rem / in.tiles_x, strip = rem - seg * in.tiles_x;
-      it.inst = i;
-      it.z = z;
-      it.x0 = strip * kRowsStrip;
-      it.ys = seg * a.tile_h;
-      it.ye = min(it.ys + a.tile_h, in.H);
-      it.W = in.W;
-      it.H = in.H;
-      it.pitch_out = in.pitch_out;
-      it.out_off = in.out_off;
-      it.seed_xor = in.seed_xor;
-      it.qa = it.ys - 2;  // box row 0 = image row ys - 2 (negative rows read the fill value)
-      it.nchunks = (it.ye - it.ys + 4 + kRowsChunk - 1) / kRowsChunk;
-      it.bx = MIR ? ((in.W - it.x0 - 126) & ~15) : ((it.x0 - 2) & ~15);
-    }
-    if (lane == 0) w.fifo[st.tail % kRowsFifo] = it;
-    st.item = st.tail;
-    st.tail += 1;
-    st.j = 0;
-    if (st.done) {
-      if (lane == 0) w.iss = st;
-      __syncwarp();
-      return;
-    }
+__device__ __noinline__ void rows_claim(const StencilArgs &a, RowWarpSmem &w, RowIssue &st, int lane) {
+  unsigned int t = 0;
+  if (lane == 0) t = atomicAdd(a.queue, 1u);
+  t = __shfl_sync(0xFFFFFFFFu, t, 0);
+  RowItem it;
+  if ((int64_t)t >= a.total_tiles) {
+    it.inst = -1;
+    it.nchunks = 0;
+    st.done = 1;
+  } else {
+    const int i = warp_find_instance(a.tile_prefix, a.ninst, (int64_t)t, lane);
+    const StencilInstance in = a.inst[i];
+    // tile index within the instance and tiles per plane both fit 32 bits
+    const int lt = (int)((int64_t)t - a.tile_prefix[i]);
+    const int per_plane = in.tiles_x * in.tiles_y;
+    const int z = lt / per_plane;
+    const int rem = lt - z * per_plane;
+    const int seg = rem / in.tiles_x, strip = rem - seg * in.tiles_x;
+    it.inst = i;
+    it.z = z;
+    it.x0 = strip * kRowsStrip;
+    it.ys = seg * a.tile_h;
+    it.ye = min(it.ys + a.tile_h, in.H);
+    it.W = in.W;
+    it.H = in.H;
+    it.pitch_out = in.pitch_out;
+    it.out_off = in.out_off;
+    it.seed_xor = in.seed_xor;
+    it.qa = it.ys - 2;  // box row 0 = image row ys - 2 (negative rows read the fill value)
+    it.nchunks = (it.ye - it.ys + 4 + kRowsChunk - 1) / kRowsChunk;
+    it.bx = MIR ? ((in.W - it.x0 - 126) & ~15) : ((it.x0 - 2) & ~15);
   }
-  const RowItem &it = w.fifo[st.item % kRowsFifo];
+  if (lane == 0) w.fifo[st.tail % kRowsFifo] = it;
+  __syncwarp();
+  st.item = st.tail;
+  st.nchunks = it.nchunks;
+  st.tail += 1;
+  st.j = 0;
+}
+
+// Starts the copy of one more chunk into the ring, claiming a new item when the current one is
+// fully issued (all lanes call it).
+template <bool MIR>
+__device__ __forceinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, RowIssue &st, int lane) {
+  if (st.done) return;
+  if (st.item < 0 || st.j == st.nchunks) {
+    rows_claim<MIR>(a, w, st, lane);
+    if (st.done) return;
+  }
   if (lane == 0) {
+    const RowItem &it = w.fifo[st.item % kRowsFifo];
     const int b = st.count % kRowsBufs;
     fence_proxy_async();
     mbar_expect_tx(&w.bar[b], kRowsBoxBytes);
@@ -518,8 +525,6 @@ __device__ __noinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, in
   }
   st.j += 1;
   st.count += 1;
-  if (lane == 0) w.iss = st;
-  __syncwarp();
 }
 
 // Bounded wait of the whole warp on chunk s's barrier; the result is the same on every lane.
@@ -600,12 +605,11 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
   if (lane == 0) {
     for (int b = 0; b < kRowsBufs; ++b) mbar_init(&w.bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    RowIssue st{};
-    st.item = -1;
-    w.iss = st;
   }
   __syncwarp();
-  for (int k = 0; k < kRowsBufs; ++k) rows_issue<MIR>(a, w, lane);
+  RowIssue st{};
+  st.item = -1;
+  for (int k = 0; k < kRowsBufs; ++k) rows_issue<MIR>(a, w, st, lane);
 
   int cur = 0;   // boxes consumed so far
   int head = 0;  // FIFO slots consumed so far
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
       if (k > 0 && (k % (kRowsChunk / kRowsGroup)) == 0) {
         __syncwarp();
         ++cur;
-        rows_issue<MIR>(a, w, lane);
+        rows_issue<MIR>(a, w, st, lane);
       }
       if (k % (kRowsChunk / kRowsGroup) == 0 && !rows_wait(w, cur, polls)) {
         failed = true;
@@ -753,14 +757,14 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
     if (failed) break;
     __syncwarp();
     ++cur;
-    rows_issue<MIR>(a, w, lane);
+    rows_issue<MIR>(a, w, st, lane);
   }
 
   if (failed) {
     if (lane == 0) {
       *(volatile unsigned int *)a.status = 1u;  // may be mapped host memory
       // let this warp's copies in flight land before it leaves (bounded as well)
-      const int issued = w.iss.count;
+      const int issued = st.count;
       for (int s = cur; s < issued; ++s)
         (void)mbar_wait_bounded(&w.bar[s % kRowsBufs], (uint32_t)(s / kRowsBufs) & 1u);
     }
