@@ -85,6 +85,36 @@ __device__ __forceinline__ void noise16(uint32_t (&w)[4], const uint32_t (&ch)[1
 template <int NN, int U>
 __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4],
                                             const uint32_t (&ch)[NN > 0 ? NN : 1][16], const uint32_t *ypre) {
+  // common sequences first: one uniform branch instead of a walk over the op list
+  const int pat = a.pattern;
+  if (pat == PAT_NONE) return;
+  if (pat == PAT_SOLARISE) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[u][j] = solarise4(w[u][j]);
+    return;
+  }
+  if (pat == PAT_THRESH) {
+    const Thresh t = make_thresh(a.pattern_t);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[u][j] = (ge4(w[u][j], t.t0, t.t0lo) >> 7) + (ge4(w[u][j], t.t1, t.t1lo) >> 7);
+    return;
+  }
+  if constexpr (NN >= 1) {
+    if (pat == PAT_NOISE || pat == PAT_NOISE_SOLARISE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        noise16(w[u], ch[0], ypre[u]);
+        if (pat == PAT_NOISE_SOLARISE)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) w[u][j] = solarise4(w[u][j]);
+      }
+      return;
+    }
+  }
   int kn = 0;
   for (int i = 0; i < a.nops; ++i) {
     const int kind = a.ops[i].kind;
@@ -407,8 +437,10 @@ int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block) {
   return c;
 }
 
-cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s) {
+cudaError_t launch_chain(const ChainArgs &ca, int n_noise, int unroll, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
+  ChainArgs a = ca;
+  a.pattern = op_pattern(a.ops, a.nops, &a.pattern_t);
   const void *fn = pick(n_noise, a.mirror != 0, unroll);
   if (!fn) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};

@@ -561,6 +561,24 @@ __device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q
     const uint32_t y = y0 + (uint32_t)j;
     yp[j] = y ^ (y >> 16);
   }
+  // common sequences first: one uniform branch instead of a walk over the op list
+  const int pat = a.pre_pattern;
+  if (pat == PAT_NONE) return;
+  if (pat == PAT_SOLARISE) {
+#pragma unroll
+    for (int j = 0; j < G; ++j) q[j] = solarise4(q[j]);
+    return;
+  }
+  if constexpr (NN >= 1) {
+    if (pat == PAT_NOISE || pat == PAT_NOISE_SOLARISE) {
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        q[j] = noise4(q[j], cpa, yp[j]);
+        if (pat == PAT_NOISE_SOLARISE) q[j] = solarise4(q[j]);
+      }
+      return;
+    }
+  }
   int kn = 0;
   for (int i = 0; i < a.npre; ++i) {
     const int kind = a.pre[i].kind;
@@ -883,9 +901,11 @@ int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps) {
   return c;
 }
 
-cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+cudaError_t launch_stencil(const StencilArgs &sa, int grid, int block, size_t smem, cudaStream_t s) {
   cudaError_t e = stencil_prepare();
   if (e != cudaSuccess) return e;
+  StencilArgs a = sa;
+  a.pre_pattern = op_pattern(a.pre, a.npre, &a.pre_pattern_t);
   void *args[] = {(void *)&a};
   if (a.rows_kernel) {
     const int nn = count_noise_ops(a.pre, a.npre);

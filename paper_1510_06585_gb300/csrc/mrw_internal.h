@@ -32,6 +32,38 @@ struct ChainOp {
 };
 
 // Fused pointwise chain over one u8 image or volume (rows of W pixels).
+// Op sequences common enough that the kernels run them without walking the op list (mirror ops,
+// which move no data, do not count). PAT_GENERIC: anything else, interpreted op by op.
+enum OpPattern : int32_t {
+  PAT_GENERIC = 0,
+  PAT_NONE = 1,
+  PAT_NOISE = 2,           // one noise op
+  PAT_SOLARISE = 3,        // one solarise op
+  PAT_NOISE_SOLARISE = 4,  // noise, then solarise
+  PAT_THRESH = 5,          // one threshold op (its thresholds in the args' pattern_t)
+};
+
+// Pattern of ops[0, n) and, for PAT_THRESH, the op's thresholds in *t (host side).
+inline int32_t op_pattern(const ChainOp *ops, int n, uint32_t *t) {
+  int idx[2], m = 0;
+  *t = 0;
+  for (int i = 0; i < n; ++i) {
+    if (ops[i].kind == OP_MIRROR) continue;
+    if (m == 2) return PAT_GENERIC;
+    idx[m++] = i;
+  }
+  if (m == 0) return PAT_NONE;
+  const int k0 = ops[idx[0]].kind;
+  if (m == 2) return k0 == OP_NOISE && ops[idx[1]].kind == OP_SOLARISE ? PAT_NOISE_SOLARISE : PAT_GENERIC;
+  if (k0 == OP_NOISE) return PAT_NOISE;
+  if (k0 == OP_SOLARISE) return PAT_SOLARISE;
+  if (k0 == OP_THRESH) {
+    *t = ops[idx[0]].t;
+    return PAT_THRESH;
+  }
+  return PAT_GENERIC;
+}
+
 struct ChainArgs {
   const uint8_t *in;
   uint8_t *out;            // nullptr: reduce only
@@ -55,6 +87,8 @@ struct ChainArgs {
   unsigned long long *partials;
   unsigned int *ticket;
   int64_t row0;            // global row of the first row (the Offset trait, for the noise hash)
+  int32_t pattern;         // OpPattern of ops[0, nops) (set by launch_chain)
+  uint32_t pattern_t;      // PAT_THRESH thresholds
   ChainOp ops[kMaxChainOps];
 };
 
@@ -102,6 +136,8 @@ struct StencilArgs {
                                     // maps' box is kRowsBoxW x kRowsChunk
   int32_t rows_cps;                 // row-streaming kernel: CTAs per SM the launch is sized for
                                     // (selects the variant budgeted for 4, or for 3, CTAs per SM)
+  int32_t pre_pattern;              // row-streaming kernel: OpPattern of pre[0, npre) (set by
+  uint32_t pre_pattern_t;           // launch_stencil) and its PAT_THRESH thresholds
   ChainOp pre[kMaxChainOps];
   ChainOp suf[kMaxChainOps];
 };
