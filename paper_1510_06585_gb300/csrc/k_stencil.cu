@@ -731,29 +731,23 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
       }
       if (k > 0) {
         uint32_t o[kRowsGroup];
-        {
-          uint32_t sa = 0x000C000Cu, sb = 0x000C000Cu, ta = 0, tb = 0;
-          uint32_t suf02[kRowsGroup], suf13[kRowsGroup];
+        // the first output row's window is rows 4k - 4 .. 4k (+12 rounds half up); each next row
+        // adds the entering row and drops the leaving one
+        uint32_t v02 = (p02[0] + p02[1] + p02[2]) + (p02[3] + h02[0] + 0x000C000Cu);
+        uint32_t v13 = (p13[0] + p13[1] + p13[2]) + (p13[3] + h13[0] + 0x000C000Cu);
 #pragma unroll
-          for (int j = kRowsGroup - 1; j >= 0; --j) {
-            sa += p02[j];
-            sb += p13[j];
-            suf02[j] = sa;
-            suf13[j] = sb;
+        for (int j = 0; j < kRowsGroup; ++j) {
+          if (j > 0) {
+            v02 += h02[j] - p02[j - 1];
+            v13 += h13[j] - p13[j - 1];
           }
-#pragma unroll
-          for (int j = 0; j < kRowsGroup; ++j) {
-            ta += h02[j];
-            tb += h13[j];
-            const uint32_t v02 = suf02[j] + ta, v13 = suf13[j] + tb;
-            // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane, as a multiplication (division by
-            // an invariant integer, Granlund and Montgomery 1994): high lane mulhi(v, 5243) >> 1,
-            // low lane the same on v << 16; 5243 = ceil(2^17 / 25), exact over the whole range of
-            // both lanes whatever the other lane holds (checked exhaustively)
-            const uint32_t d0 = __umulhi(v02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(v02, 5243u) >> 1;
-            const uint32_t d1 = __umulhi(v13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(v13, 5243u) >> 1;
-            o[j] = d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u;
-          }
+          // x / 25 for x <= 25 * 255 + 12 in either 16-bit lane, as a multiplication (division by
+          // an invariant integer, Granlund and Montgomery 1994): high lane mulhi(v, 5243) >> 1,
+          // low lane the same on v << 16; 5243 = ceil(2^17 / 25), exact over the whole range of
+          // both lanes whatever the other lane holds (checked exhaustively)
+          const uint32_t d0 = __umulhi(v02 * 0x10000u, 5243u) >> 1, d2 = __umulhi(v02, 5243u) >> 1;
+          const uint32_t d1 = __umulhi(v13 * 0x10000u, 5243u) >> 1, d3 = __umulhi(v13, 5243u) >> 1;
+          o[j] = d0 + d1 * 0x100u + d2 * 0x10000u + d3 * 0x1000000u;
         }
         const int nrow = min(kRowsGroup, nv - 4 * k);  // output rows of this group (1..4)
         if (nrow == kRowsGroup && L.nout == 4) {

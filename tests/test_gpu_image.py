@@ -63,6 +63,23 @@ def test_random_chains_match_depth_first_oracle(seed):
         assert np.array_equal(got, want), (names, h, w)
 
 
+@pytest.mark.parametrize("names", [
+    ["noise"], ["solarise"], ["threshold3"], ["noise", "solarise"], ["mirror", "noise", "mirror", "solarise"],
+    ["solarise", "noise"], ["noise", "solarise", "mirror", "solarise"], ["threshold3", "solarise"], ["mirror"],
+])
+def test_op_sequences_with_and_without_fast_paths(names):
+    # the kernels run the common sequences (one noise, one solarise, one threshold, noise then
+    # solarise; mirrors do not count) without walking the op list; near misses take the general path
+    seeds = {i: 40 + i for i in range(len(names))}
+    tree = build_image_tree(names, seeds)
+    for (h, w) in [(37, 301), (64, 1024), (5, 17)]:
+        img = inputs.filter_image(h, w, seed=h * w)
+        want, _ = S.evaluate_image(oracle_tree(names, seeds), img)
+        for cfg in (M.config(), M.config(unroll=1), M.config(unroll=4), M.config(unroll=8)):
+            got, _ = run_image(tree, img, cfg)
+            assert np.array_equal(got, want), (names, h, w, cfg.as_tuple())
+
+
 def test_every_candidate_config_gives_the_same_bytes():
     img = inputs.filter_image(333, 517, seed=5)
     tree = build_image_tree(["noise", "mirror", "solarise", "noise"], {0: 3, 3: 4})

@@ -48,6 +48,12 @@ def test_stencil_prefix_suffix_orders(names):
     FILTER_BLUR,
     ["noise", "mirror", "noise", "solarise", "blur5"],
     ["threshold3", "mirror", "blur5"],
+    # each prefix sequence the kernel runs without walking the op list, and near misses of them
+    ["noise", "blur5"],
+    ["solarise", "mirror", "blur5"],
+    ["mirror", "noise", "mirror", "solarise", "blur5"],
+    ["solarise", "noise", "blur5"],
+    ["noise", "solarise", "solarise", "blur5"],
 ])
 def test_row_streaming_blur_strip_and_segment_edges(names):
     # blur groups with only a prefix run on the row-streaming kernel: strips of 124 output columns,
