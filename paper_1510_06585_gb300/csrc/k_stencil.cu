@@ -431,18 +431,20 @@ struct RowItem {
 };
 
 // Issue-side state of a warp: every lane holds the same copy in registers (the lanes run the
-// issue path together; lane 0 alone writes shared memory and starts the copies).
+// issue path together; lane 0 alone writes shared memory and starts the copies). The item being
+// issued is in FIFO slot (tail - 1) % kRowsFifo.
 struct RowIssue {
-  int32_t item;     // FIFO slot of the item being issued (-1: none)
-  int32_t j;        // next chunk of that item
-  int32_t nchunks;  // chunks of that item
+  int32_t j;        // next chunk of the item being issued
+  int32_t nchunks;  // chunks of that item (-1: the tile counter is exhausted)
   int32_t count;    // chunks issued so far
   int32_t tail;     // FIFO slots written so far
-  int32_t done;     // the tile counter is exhausted
 };
 
 struct alignas(128) RowWarpSmem {
   uint8_t buf[kRowsBufs][kRowsChunk][kRowsBoxW];
+  // column halves of each noise op's hashes for lane l's 4 Q columns (written and read by lane l
+  // only; kept here rather than in registers, which the row loop needs)
+  uint4 cp[kMaxNoisePerGroup][32];
   uint64_t bar[kRowsBufs];
   RowItem fifo[kRowsFifo];
 };
@@ -464,18 +466,19 @@ __device__ __forceinline__ int warp_find_instance(const int64_t *prefix, int nin
   return lo;
 }
 
-// Claims the next work item from the tile counter and decodes it into the next FIFO slot (all
-// lanes call it; lane 0 writes the slot).
+// Claims the next work item from the tile counter and decodes it into FIFO slot `slot` (all lanes
+// call it; lane 0 writes the slot). Returns the item's chunk count, or -1 when the counter is
+// exhausted (the slot then holds the end marker). The issue state stays in the caller's registers:
+// a reference to it here would put it in local memory.
 template <bool MIR>
-__device__ __noinline__ void rows_claim(const StencilArgs &a, RowWarpSmem &w, RowIssue &st, int lane) {
+__device__ __noinline__ int rows_claim(const StencilArgs &a, RowWarpSmem &w, int slot, int lane) {
   unsigned int t = 0;
   if (lane == 0) t = atomicAdd(a.queue, 1u);
   t = __shfl_sync(0xFFFFFFFFu, t, 0);
   RowItem it;
   if ((int64_t)t >= a.total_tiles) {
     it.inst = -1;
-    it.nchunks = 0;
-    st.done = 1;
+    it.nchunks = -1;
   } else {
     const int i = warp_find_instance(a.tile_prefix, a.ninst, (int64_t)t, lane);
     const StencilInstance in = a.inst[i];
@@ -499,25 +502,24 @@ __device__ __noinline__ void rows_claim(const StencilArgs &a, RowWarpSmem &w, Ro
     it.nchunks = (it.ye - it.ys + 4 + kRowsChunk - 1) / kRowsChunk;
     it.bx = MIR ? ((in.W - it.x0 - 126) & ~15) : ((it.x0 - 2) & ~15);
   }
-  if (lane == 0) w.fifo[st.tail % kRowsFifo] = it;
+  if (lane == 0) w.fifo[slot] = it;
   __syncwarp();
-  st.item = st.tail;
-  st.nchunks = it.nchunks;
-  st.tail += 1;
-  st.j = 0;
+  return it.nchunks;
 }
 
 // Starts the copy of one more chunk into the ring, claiming a new item when the current one is
 // fully issued (all lanes call it).
 template <bool MIR>
 __device__ __forceinline__ void rows_issue(const StencilArgs &a, RowWarpSmem &w, RowIssue &st, int lane) {
-  if (st.done) return;
-  if (st.item < 0 || st.j == st.nchunks) {
-    rows_claim<MIR>(a, w, st, lane);
-    if (st.done) return;
+  if (st.nchunks < 0) return;
+  if (st.j == st.nchunks) {  // the item is fully issued (or none was claimed yet)
+    st.nchunks = rows_claim<MIR>(a, w, st.tail % kRowsFifo, lane);
+    st.tail += 1;
+    st.j = 0;
+    if (st.nchunks < 0) return;
   }
   if (lane == 0) {
-    const RowItem &it = w.fifo[st.item % kRowsFifo];
+    const RowItem &it = w.fifo[(st.tail - 1) % kRowsFifo];
     const int b = st.count % kRowsBufs;
     fence_proxy_async();
     mbar_expect_tx(&w.bar[b], kRowsBoxBytes);
@@ -553,8 +555,7 @@ __device__ __forceinline__ uint32_t rows_quad(const uint8_t *row, const RowLane 
 // Prefix ops on the lane's quads of G consecutive source rows (row j's hash row is y0 + j): each
 // op is decoded once for the G rows, whose 4 G pixels are independent work for the scheduler.
 template <int NN, int G>
-__device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q)[G], const uint32_t (&cpa)[4],
-                                              const uint32_t (&cpb)[4], uint32_t y0) {
+__device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q)[G], const uint4 *cp, uint32_t y0) {
   uint32_t yp[G];
 #pragma unroll
   for (int j = 0; j < G; ++j) {
@@ -571,9 +572,10 @@ __device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q
   }
   if constexpr (NN >= 1) {
     if (pat == PAT_NOISE || pat == PAT_NOISE_SOLARISE) {
+      const uint4 c = cp[0];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
-        q[j] = noise4(q[j], cpa, yp[j]);
+        q[j] = noise4(q[j], c.x, c.y, c.z, c.w, yp[j]);
         if (pat == PAT_NOISE_SOLARISE) q[j] = solarise4(q[j]);
       }
       return;
@@ -593,14 +595,10 @@ __device__ __forceinline__ void rows_prefix_g(const StencilArgs &a, uint32_t (&q
         q[j] = (ge4(q[j], t0, t0 & 0x7F7F7F7Fu) >> 7) + (ge4(q[j], t1, t1 & 0x7F7F7F7Fu) >> 7);
     } else if (kind == OP_NOISE) {
       if constexpr (NN >= 1) {
-        if (kn == 0) {
+        if (kn < NN) {
+          const uint4 c = cp[kn * 32];
 #pragma unroll
-          for (int j = 0; j < G; ++j) q[j] = noise4(q[j], cpa, yp[j]);
-        } else {
-          if constexpr (NN >= 2) {
-#pragma unroll
-            for (int j = 0; j < G; ++j) q[j] = noise4(q[j], cpb, yp[j]);
-          }
+          for (int j = 0; j < G; ++j) q[j] = noise4(q[j], c.x, c.y, c.z, c.w, yp[j]);
         }
       }
       ++kn;
@@ -618,15 +616,13 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   RowWarpSmem &w = reinterpret_cast<RowWarpSmem *>(smem)[threadIdx.x >> 5];
-  const uint32_t polls = a.wait_polls ? a.wait_polls - 1 : kWaitPolls;
 
   if (lane == 0) {
     for (int b = 0; b < kRowsBufs; ++b) mbar_init(&w.bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  RowIssue st{};
-  st.item = -1;
+  RowIssue st{};  // j == nchunks == 0: the first call claims an item
   for (int k = 0; k < kRowsBufs; ++k) rows_issue<MIR>(a, w, st, lane);
 
   int cur = 0;   // boxes consumed so far
@@ -636,7 +632,6 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
     const RowItem &it = w.fifo[head % kRowsFifo];
     ++head;
     if (it.inst < 0) break;
-    uint32_t cpa[4] = {0, 0, 0, 0}, cpb[4] = {0, 0, 0, 0};
     RowLane L;
     {
       const int W = it.W;
@@ -648,15 +643,14 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
           if (a.pre[i].kind != OP_NOISE) continue;
           const uint32_t fs = fmix32(a.pre[i].seed ^ it.seed_xor);
           const int flip = a.pre[i].flip;
+          uint32_t v[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int cc = min(max(c0 + k, 0), W - 1);
             const uint32_t c = fmix32(fs ^ (uint32_t)(flip ? W - 1 - cc : cc));
-            if (kn == 0) cpa[k] = c ^ (c >> 16);
-            if constexpr (NN >= 2) {
-              if (kn == 1) cpb[k] = c ^ (c >> 16);
-            }
+            v[k] = c ^ (c >> 16);
           }
+          w.cp[kn][lane] = make_uint4(v[0], v[1], v[2], v[3]);
           ++kn;
         }
       }
@@ -692,7 +686,7 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
         ++cur;
         rows_issue<MIR>(a, w, st, lane);
       }
-      if (k % (kRowsChunk / kRowsGroup) == 0 && !rows_wait(w, cur, polls)) {
+      if (k % (kRowsChunk / kRowsGroup) == 0 && !rows_wait(w, cur, a.wait_polls ? a.wait_polls - 1 : kWaitPolls)) {
         failed = true;
         break;
       }
@@ -700,7 +694,7 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
       uint32_t q[kRowsGroup];
 #pragma unroll
       for (int j = 0; j < kRowsGroup; ++j) q[j] = rows_quad(box + j * kRowsBoxW, L);
-      rows_prefix_g<NN, kRowsGroup>(a, q, cpa, cpb, L.yrow + (uint32_t)(4 * k));
+      rows_prefix_g<NN, kRowsGroup>(a, q, &w.cp[0][lane], L.yrow + (uint32_t)(4 * k));
       uint32_t h02[kRowsGroup], h13[kRowsGroup];
 #pragma unroll
       for (int j = 0; j < kRowsGroup; ++j) {
