@@ -191,6 +191,23 @@ const char *mrw_status_string(mrw_status s);
 /* ------------------------------------------------------------------------------------------ */
 /* A leaf: one kernel stage. `params` may be NULL (all defaults). */
 mrw_status mrw_stage(mrw_stage_kind kind, const mrw_stage_params *params, mrw_node_t *out);
+/* A leaf whose kernel the programmer writes (Section 2: the leaves of an SCT are user kernels): a u8
+ * image stage given as CUDA C source that defines
+ *     __device__ unsigned char <name>(unsigned char p, int x, int y, const unsigned int *u);
+ * which maps the pixel p at column x and row y of the stage's input (global coordinates: rows of a
+ * volume are counted across its planes, as for the noise stage; a mirror before the stage flips x)
+ * to the stage's output pixel; u points at the 8 values of `params` (NULL: zeros). The function must
+ * be pointwise and may call only device code it defines itself. `name` is a C identifier; `source`
+ * and `name` are copied. The source is compiled here once as a check, with NVRTC (the CUDA
+ * toolkit's run-time compiler, opened on first use); at execution, each group of consecutive
+ * pointwise stages containing user stages (a blur ends a group) is compiled into one kernel that
+ * applies all of them in registers, cached per generated source and device. User stages run in
+ * mrw_execute on image trees (Map, Pipeline, Loop FOR, MapReduce over them); the batched calls and
+ * WHILE_CHANGED loops return MRW_ERR_UNSUPPORTED for trees that contain one.
+ * Errors: MRW_ERR_INVALID_ARG (NULL or empty argument, `name` not an identifier or longer than
+ * 63 characters, `source` longer than 64 KiB); MRW_ERR_UNSUPPORTED (NVRTC not found, or the source
+ * does not compile: mrw_last_error() holds the compiler's log). */
+mrw_status mrw_stage_user(const char *name, const char *source, const uint32_t *params, mrw_node_t *out);
 /* An empty Pipeline: a chain of control- and data-dependent subtrees (Section 2.1). */
 mrw_status mrw_pipeline_create(mrw_node_t *out);
 /* Append a new leaf stage to a pipeline. */

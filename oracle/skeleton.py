@@ -20,6 +20,10 @@ Trees are plain tuples:
     ("loop", child, iters)
     ("loop_while", child, max_iters) repeat while the last run changed its input (at most
                                 max_iters runs): a convergence loop on image trees
+    ("user", fn)                a user-defined stage (Section 2: the leaves of an SCT are
+                                the programmer's kernels): fn(img, y0) returns the stage's
+                                output for one plane whose first row has global index y0; the
+                                caller writes fn as the plain definition of its kernel
 
 Every intermediate is materialised; ``trace`` records the leaves in the order
 they ran. Parity is pinned by tests/test_oracle_skeleton.py (stage order with
@@ -40,6 +44,13 @@ def evaluate_image(tree, img: np.ndarray, trace: list | None = None, y0: int = 0
         if trace is not None:
             trace.append(name)
         return image.apply_stage(name, img, seed=params.get("seed", 0), y0=y0), None
+    if kind == "user":
+        if trace is not None:
+            trace.append("user")
+        if img.ndim == 3:  # a stage sees the rows of a volume as one image, counted across planes
+            d, h, w = img.shape
+            return np.asarray(tree[1](img.reshape(d * h, w), y0), dtype=np.uint8).reshape(d, h, w), None
+        return np.asarray(tree[1](img, y0), dtype=np.uint8), None
     if kind == "pipeline":
         red = None
         for child in tree[1]:
@@ -82,6 +93,8 @@ def evaluate_image(tree, img: np.ndarray, trace: list | None = None, y0: int = 0
 def _last_stage(tree):
     if tree[0] == "stage":
         return tree[1]
+    if tree[0] == "user":
+        return "user"
     if tree[0] == "pipeline":
         return _last_stage(tree[1][-1])
     if tree[0] in ("map", "mapreduce", "loop"):

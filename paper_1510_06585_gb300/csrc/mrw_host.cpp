@@ -12,12 +12,14 @@
 //   Cost model — a small MLP trained on the tuner's timings that derives a configuration for an
 //              unseen pair (replacing the interpolation of Section 3.2, Configuration Derivation).
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cctype>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -74,6 +76,7 @@ std::mutex g_mu;  // guards the caches below
 
 struct DeviceInfo {
   int sms = 0;
+  int arch = 0;  // compute capability major * 10 + minor
 };
 DeviceInfo device_info(int dev) {
   static std::map<int, DeviceInfo> cache;
@@ -83,6 +86,10 @@ DeviceInfo device_info(int dev) {
   DeviceInfo d;
   cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
   if (d.sms <= 0) d.sms = 1;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  d.arch = major * 10 + minor;
   cache[dev] = d;
   return d;
 }
@@ -262,11 +269,18 @@ mrw_status side_streams(int dev, cudaStream_t *in, cudaStream_t *out) {
 // ============================================================================================
 enum NodeKind { N_STAGE = 0, N_PIPELINE = 1, N_MAP = 2, N_MAPREDUCE = 3, N_LOOP = 4 };
 
+// A user-defined stage's device function (mrw_stage_user).
+struct mrw_user_fn {
+  std::string name, source;
+};
+
 struct mrw_node {
   std::atomic<int> refs{1};
   NodeKind kind = N_STAGE;
   mrw_stage_kind stage = MRW_ST_NOISE_HASH;
   mrw_stage_params params{};
+  std::shared_ptr<const mrw_user_fn> user;  // set for a user-defined stage
+  uint32_t uparams[kUserParams] = {};
   std::vector<mrw_node *> kids;
   mrw_reduce_op op = MRW_RED_ADD;
   mrw_loop_state loop{};
@@ -323,6 +337,16 @@ void signature(const mrw_node *n, std::string &s) {
   switch (n->kind) {
     case N_STAGE: {
       const mrw_stage_params &p = n->params;
+      if (n->user) {
+        snprintf(buf, sizeof buf, "U%zx{", std::hash<std::string>()(n->user->name + '\n' + n->user->source));
+        s += buf;
+        for (int i = 0; i < kUserParams; ++i) {
+          snprintf(buf, sizeof buf, "%s%u", i ? "," : "", n->uparams[i]);
+          s += buf;
+        }
+        s += "}";
+        return;
+      }
       snprintf(buf, sizeof buf, "S%d{%u,%d,%d,%a,%a,%a,%a,%d,%d}", (int)n->stage, p.seed, p.t0, p.t1, p.G, p.eps,
                p.dt, p.alpha, p.nu, p.wg);
       s += buf;
@@ -350,6 +374,8 @@ struct ImgStage {
   uint32_t seed;
   uint32_t t;
   int nu, wg;
+  std::shared_ptr<const mrw_user_fn> fn = nullptr;  // OP_USER: the device function
+  std::array<uint32_t, kUserParams> up = {};        // OP_USER: its parameters
 };
 
 struct NbStep {
@@ -407,6 +433,16 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
       const mrw_stage_params &q = n->params;
       if (q.nu < 0 || q.wg < 0 || (q.wg && (q.wg % 32 || q.wg > 1024)))
         return fail(MRW_ERR_CONSTRAINT, "stage %d: wg must be a multiple of 32 up to 1024", (int)n->stage);
+      if (n->user) {
+        TRY(set_family(p, F_IMAGE));
+        if ((int64_t)p.img.size() >= MRW_MAX_STAGES)
+          return fail(MRW_ERR_UNSUPPORTED, "more than %d image stages after unrolling loops", MRW_MAX_STAGES);
+        ImgStage st{OP_USER, 0, 0, q.nu, q.wg};
+        st.fn = n->user;
+        std::copy(n->uparams, n->uparams + kUserParams, st.up.begin());
+        p.img.push_back(st);
+        return MRW_OK;
+      }
       const int ok = op_kind_of(n->stage);
       if (ok >= 0) {
         TRY(set_family(p, F_IMAGE));
@@ -472,6 +508,8 @@ mrw_status flatten(const mrw_node *n, Program &p, int depth, bool is_root, int64
         TRY(flatten(n->kids[0], probe, depth + 1, false, 1));
         if (probe.fam != F_IMAGE || probe.while_begin >= 0)
           return fail(MRW_ERR_UNSUPPORTED, "WHILE_CHANGED loops run image trees");
+        for (const ImgStage &st : probe.img)
+          if (st.kind == OP_USER) return fail(MRW_ERR_UNSUPPORTED, "user-defined stages inside a WHILE_CHANGED loop");
         TRY(set_family(p, F_IMAGE));
         p.while_begin = (int)p.img.size();
         TRY(flatten(n->kids[0], p, depth + 1, false, 1));
@@ -694,6 +732,7 @@ mrw_status copy_back(Launch &L) {
 // ============================================================================================
 struct Group {
   bool use_stencil = false;  // run by the stencil kernel (it has the blur, or the call is batched)
+  bool user = false;         // has user-defined stages: a pointwise group compiled at run time
   bool blur = false;
   std::vector<ImgStage> pre, suf;  // pointwise stages before / after the blur
   int reduce = RED_NONE;           // fused MapReduce (chain groups only)
@@ -721,6 +760,7 @@ std::vector<Group> group_stages(const Program &p, bool fused, bool batched) {
     for (const ImgStage &s : p.img) {
       Group g;
       g.use_stencil = batched || s.kind == OP_BLUR;
+      g.user = s.kind == OP_USER;
       g.blur = s.kind == OP_BLUR;
       if (!g.blur) g.pre.push_back(s);
       gs.push_back(g);
@@ -736,7 +776,7 @@ std::vector<Group> group_stages(const Program &p, bool fused, bool batched) {
     for (const ImgStage &s : p.img) {
       if (!open) fresh();
       if (s.kind == OP_BLUR) {
-        if (cur.blur) {
+        if (cur.blur || cur.user) {  // user stages never run inside the blur kernels
           gs.push_back(cur);
           fresh();
         }
@@ -744,14 +784,20 @@ std::vector<Group> group_stages(const Program &p, bool fused, bool batched) {
         cur.use_stencil = true;
         continue;
       }
+      if (s.kind == OP_USER && cur.blur) {
+        gs.push_back(cur);
+        fresh();
+      }
       std::vector<ImgStage> &list = cur.blur ? cur.suf : cur.pre;
       const bool full = (int)list.size() >= kMaxChainOps ||
-                        (!cur.use_stencil && s.kind == OP_NOISE && count_noise(cur.pre) >= kMaxNoisePerGroup);
+                        (!cur.use_stencil && !cur.user && s.kind == OP_NOISE &&
+                         count_noise(cur.pre) >= kMaxNoisePerGroup);
       if (full) {
         gs.push_back(cur);
         fresh();
       }
       (cur.blur ? cur.suf : cur.pre).push_back(s);
+      cur.user = cur.user || s.kind == OP_USER;
     }
     if (open) gs.push_back(cur);
   }
@@ -761,7 +807,7 @@ std::vector<Group> group_stages(const Program &p, bool fused, bool batched) {
     gs.push_back(g);
   }
   if (p.reduce != RED_NONE) {
-    if (fused && !gs.back().use_stencil) {
+    if (fused && !gs.back().use_stencil && !gs.back().user) {
       gs.back().reduce = p.reduce;
     } else {
       Group r;
@@ -1079,6 +1125,150 @@ ImgGeom geom_of(const mrw_buffer &b, const View &v) {
 
 // Run `gs` from src to dst: groups in order, intermediates in (at most two) stream-ordered
 // scratch images; a reduce-only group reads the previous group's output.
+// ---- groups with user-defined stages: one kernel generated per group and compiled at run time ----
+
+// Source of the kernel for a pointwise group with user stages. A thread owns a 16-pixel segment of
+// one row; each pixel goes through the group's stages in registers. The built-in stages are
+// restated per pixel (noise: clamp(p + F(F(F(seed) ^ x) ^ y) mod 41 - 20) with F the MurmurHash3
+// finaliser; solarise; threshold), the user functions each sit in a namespace of their own, and a
+// mirror only flips the column coordinate of the stages after it (as in the chain kernel). All
+// numeric parameters are kernel arguments, so the source depends only on the stage kinds, the
+// mirrors and the user functions.
+std::string user_chain_source(const Group &g) {
+  const int parity = mirror_parity(g.pre);
+  std::ostringstream o;
+  o << "typedef unsigned int u32;\ntypedef unsigned char u8;\n"
+    << "struct MrwUserArgs { " << kUserArgsFields << " };\n"
+    << "__device__ __forceinline__ u32 mrw_fmix32(u32 h) {\n"
+    << "  h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;\n  return h;\n}\n";
+  int nu = 0;
+  for (const ImgStage &st : g.pre)
+    if (st.kind == OP_USER) o << "namespace mrw_user_" << nu++ << " {\n" << st.fn->source << "\n}\n";
+  o << "__device__ __forceinline__ void mrw_unpack(u32 w, u8 *b) {\n"
+    << "  b[0] = (u8)w; b[1] = (u8)(w >> 8); b[2] = (u8)(w >> 16); b[3] = (u8)(w >> 24);\n}\n"
+    << "__device__ __forceinline__ u32 mrw_pack(const u8 *b) {\n"
+    << "  return (u32)b[0] | (u32)b[1] << 8 | (u32)b[2] << 16 | (u32)b[3] << 24;\n}\n"
+    << "extern \"C\" __global__ void __launch_bounds__(256) mrw_user_chain(const MrwUserArgs a) {\n"
+    << "  const int W = a.W, segs = (W + 15) >> 4;\n"
+    << "  const long long total = a.rows * segs, stride = (long long)gridDim.x * blockDim.x;\n"
+    << "  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {\n"
+    << "    const long long y = t / segs;\n"
+    << "    const int x0 = (int)(t - y * segs) * 16, n = W - x0 < 16 ? W - x0 : 16;\n"
+    << "    const u8 *src = a.in + y * a.in_pitch;\n"
+    << "    u8 *dst = a.out + y * a.out_pitch;\n"
+    << "    const u32 yg = (u32)(y + a.row0);\n"
+    << "    u8 v[16];\n";
+  if (!parity) {
+    o << "    if (n == 16) {\n"
+      << "      const uint4 q = *reinterpret_cast<const uint4 *>(src + x0);\n"
+      << "      mrw_unpack(q.x, v); mrw_unpack(q.y, v + 4); mrw_unpack(q.z, v + 8); mrw_unpack(q.w, v + 12);\n"
+      << "    } else {\n"
+      << "#pragma unroll\n"
+      << "      for (int k = 0; k < 16; ++k) v[k] = k < n ? src[x0 + k] : (u8)0;\n"
+      << "    }\n";
+  } else {
+    o << "    if (n == 16 && (W & 15) == 0) {\n"
+      << "      const uint4 q = *reinterpret_cast<const uint4 *>(src + (W - x0 - 16));\n"
+      << "      u8 r[16];\n"
+      << "      mrw_unpack(q.x, r); mrw_unpack(q.y, r + 4); mrw_unpack(q.z, r + 8); mrw_unpack(q.w, r + 12);\n"
+      << "#pragma unroll\n"
+      << "      for (int k = 0; k < 16; ++k) v[k] = r[15 - k];\n"
+      << "    } else {\n"
+      << "#pragma unroll\n"
+      << "      for (int k = 0; k < 16; ++k) v[k] = k < n ? src[W - 1 - (x0 + k)] : (u8)0;\n"
+      << "    }\n";
+  }
+  o << "#pragma unroll\n"
+    << "    for (int k = 0; k < 16; ++k) {\n"
+    << "      if (k >= n) continue;\n"
+    << "      const int x = x0 + k;\n"
+    << "      u32 p = v[k];\n";
+  int before = 0, ui = 0;
+  for (size_t i = 0; i < g.pre.size(); ++i) {
+    const ImgStage &st = g.pre[i];
+    const bool flip = (parity ^ (before & 1)) != 0;
+    const char *col = flip ? "(W - 1 - x)" : "x";
+    switch (st.kind) {
+      case OP_MIRROR: ++before; break;
+      case OP_NOISE:
+        o << "      { const u32 h = mrw_fmix32(mrw_fmix32(mrw_fmix32(a.p[" << i << "][0]) ^ (u32)" << col
+          << ") ^ yg); const int q = (int)p + (int)(h % 41u) - 20; p = q < 0 ? 0u : (q > 255 ? 255u : (u32)q); }\n";
+        break;
+      case OP_SOLARISE: o << "      p = p < 128u ? p : 255u - p;\n"; break;
+      case OP_THRESH: o << "      p = (u32)(p >= a.p[" << i << "][0]) + (u32)(p >= a.p[" << i << "][1]);\n"; break;
+      case OP_USER:
+        o << "      p = (u32)mrw_user_" << ui++ << "::" << st.fn->name << "((u8)p, " << col << ", (int)yg, a.p[" << i
+          << "]);\n";
+        break;
+      default: break;
+    }
+  }
+  o << "      v[k] = (u8)p;\n"
+    << "    }\n"
+    << "    if (n == 16) {\n"
+    << "      uint4 q;\n"
+    << "      q.x = mrw_pack(v); q.y = mrw_pack(v + 4); q.z = mrw_pack(v + 8); q.w = mrw_pack(v + 12);\n"
+    << "      *reinterpret_cast<uint4 *>(dst + x0) = q;\n"
+    << "    } else {\n"
+    << "#pragma unroll\n"
+    << "      for (int k = 0; k < 16; ++k)\n"
+    << "        if (k < n) dst[x0 + k] = v[k];\n"
+    << "    }\n"
+    << "  }\n"
+    << "}\n";
+  return o.str();
+}
+
+// The compiled kernel of a user group on the launch's device (compiled on first use, then cached).
+mrw_status user_chain_kernel(const Launch &L, const Group &g, cudaKernel_t *k) {
+  std::string err;
+  if (!jit_kernel(user_chain_source(g), "mrw_user_chain", L.device, device_info(L.device).arch, k, &err))
+    return fail(MRW_ERR_UNSUPPORTED, "%s", err.c_str());
+  return MRW_OK;
+}
+
+// Compiles the kernels of every user group before anything is launched, so that a compile or load
+// error leaves nothing enqueued.
+mrw_status prepare_user_groups(const Launch &L, const std::vector<Group> &gs) {
+  for (const Group &g : gs) {
+    if (!g.user) continue;
+    cudaKernel_t k;
+    TRY(user_chain_kernel(L, g, &k));
+  }
+  return MRW_OK;
+}
+
+mrw_status run_user_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, int64_t op,
+                          const ImgGeom &geo, const mrw_config &cfg, int64_t row0) {
+  cudaKernel_t k;
+  TRY(user_chain_kernel(L, g, &k));
+  UserChainArgs a{};
+  a.in = in;
+  a.out = out;
+  a.in_pitch = ip;
+  a.out_pitch = op;
+  a.rows = geo.rows;
+  a.row0 = row0;
+  a.W = (int)geo.W;
+  for (size_t i = 0; i < g.pre.size(); ++i) {
+    const ImgStage &st = g.pre[i];
+    if (st.kind == OP_NOISE) a.p[i][0] = st.seed;
+    if (st.kind == OP_THRESH) {
+      a.p[i][0] = st.t & 0xFF;
+      a.p[i][1] = (st.t >> 8) & 0xFF;
+    }
+    if (st.kind == OP_USER)
+      for (int j = 0; j < kUserParams; ++j) a.p[i][j] = st.up[j];
+  }
+  const int block = cfg.block > 0 ? cfg.block : 256;
+  const int cps = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 8;
+  const int64_t work = geo.rows * ((geo.W + 15) / 16);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((work + block - 1) / block, (int64_t)L.sms * cps));
+  void *args[] = {(void *)&a};
+  CU(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(block), args, 0, L.stream));
+  return MRW_OK;
+}
+
 mrw_status run_groups(Launch &L, const std::vector<Group> &gs, const uint8_t *src, int64_t sp, uint8_t *dst,
                       int64_t dp_final, const ImgGeom &geo, const mrw_config &cfg, int wg, unsigned int *status,
                       bool *used_status, unsigned long long *red) {
@@ -1099,7 +1289,9 @@ mrw_status run_groups(Launch &L, const std::vector<Group> &gs, const uint8_t *sr
     const bool last = k == n_out_groups;
     uint8_t *d = last ? dst : (uint8_t *)tmp[(k - 1) & 1];
     const int64_t dp = last ? dp_final : tpitch;
-    if (g.use_stencil) {
+    if (g.user) {
+      TRY(run_user_chain(L, g, src, sp, d, dp, geo, cfg, 0));
+    } else if (g.use_stencil) {
       TRY(run_stencil_single(L, g, src, sp, d, dp, geo, cfg, status));
       *used_status = true;
     } else {
@@ -1383,6 +1575,11 @@ std::string image_program_key(const Program &p, const ImgGeom &geo, const mrw_co
 
 mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, const View &vout, const ImgGeom &geo,
                                const mrw_config &cfg, unsigned int *status, bool *used_status) {
+  const bool fused = cfg.fusion == MRW_FUSE_ALL;
+  const Program pre = sub_program(p, 0, p.while_begin);
+  const Program post = sub_program(p, p.while_end, (int)p.img.size());
+  TRY(prepare_user_groups(L, group_stages(pre, fused, false)));  // user stages before / after the loop
+  TRY(prepare_user_groups(L, group_stages(post, fused, false)));
   const std::string key = image_program_key(p, geo, cfg, L.device, L.stream);
   WhilePlan wp;
   {
@@ -1408,9 +1605,6 @@ mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, con
   int64_t pin, pout;
   TRY(resolve(L, vin, true, false, &din, &pin));
   TRY(resolve(L, vout, false, true, &dout, &pout));
-  const bool fused = cfg.fusion == MRW_FUSE_ALL;
-  const Program pre = sub_program(p, 0, p.while_begin);
-  const Program post = sub_program(p, p.while_end, (int)p.img.size());
   if (pre.img.empty()) {
     CU(cudaMemcpy2DAsync(wp.A, wp.pitch, din, pin, geo.W, geo.rows, cudaMemcpyDeviceToDevice, L.stream));
   } else {
@@ -1438,7 +1632,8 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
   const ImgGeom geo = geom_of(args[0], vin);
   if (p.while_begin >= 0) return enqueue_image_while(L, p, vin, vout, geo, cfg, status, used_status);
   const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
-  const bool one_chain = gs.size() == 1 && !gs[0].use_stencil && vin.b->memory == MRW_MEM_HOST &&
+  TRY(prepare_user_groups(L, gs));
+  const bool one_chain = gs.size() == 1 && !gs[0].use_stencil && !gs[0].user && vin.b->memory == MRW_MEM_HOST &&
                          vout.b->memory == MRW_MEM_HOST;
   void *din = nullptr, *dout = nullptr;
   int64_t pin = vin.pitch, pout = vout.pitch;
@@ -1873,6 +2068,42 @@ mrw_status mrw_stage(mrw_stage_kind kind, const mrw_stage_params *params, mrw_no
   return MRW_OK;
 }
 
+mrw_status mrw_stage_user(const char *name, const char *source, const uint32_t *params, mrw_node_t *out) {
+  if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!name || !source || !*name || !*source) return fail(MRW_ERR_INVALID_ARG, "name and source must be non-empty");
+  const size_t nl = strlen(name);
+  bool ident = nl <= 63 && (isalpha((unsigned char)name[0]) || name[0] == '_');
+  for (size_t i = 1; ident && i < nl; ++i) ident = isalnum((unsigned char)name[i]) || name[i] == '_';
+  if (!ident) return fail(MRW_ERR_INVALID_ARG, "stage name must be a C identifier of at most 63 characters");
+  if (strlen(source) > (64u << 10)) return fail(MRW_ERR_INVALID_ARG, "user stage source above 64 KiB");
+  auto fn = std::make_shared<mrw_user_fn>();
+  fn->name = name;
+  fn->source = source;
+  // compile the function once inside a one-stage group, for the current device's architecture
+  // (sm_103 when no device is visible), so that errors surface here and not at execution
+  int dev = 0, arch = 103;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    const int a = device_info(dev).arch;
+    if (a > 0) arch = a;
+  } else {
+    cudaGetLastError();
+  }
+  Group g;
+  g.user = true;
+  ImgStage st{OP_USER, 0, 0, 0, 0};
+  st.fn = fn;
+  g.pre.push_back(st);
+  std::string err;
+  if (!jit_check(user_chain_source(g), arch, &err)) return fail(MRW_ERR_UNSUPPORTED, "%s", err.c_str());
+  mrw_node *n = new_node(N_STAGE);
+  if (!n) return fail(MRW_ERR_OOM, "node");
+  n->user = fn;
+  if (params) std::copy(params, params + kUserParams, n->uparams);
+  *out = n;
+  return MRW_OK;
+}
+
 mrw_status mrw_pipeline_create(mrw_node_t *out) {
   if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
   *out = new_node(N_PIPELINE);
@@ -2189,6 +2420,8 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
   if (p.fam != F_IMAGE) return fail(MRW_ERR_UNSUPPORTED, "batched execution runs image trees");
   if (p.reduce != RED_NONE) return fail(MRW_ERR_UNSUPPORTED, "batched MapReduce");
   if (p.while_begin >= 0) return fail(MRW_ERR_UNSUPPORTED, "batched WHILE_CHANGED loops");
+  for (const ImgStage &st : p.img)
+    if (st.kind == OP_USER) return fail(MRW_ERR_UNSUPPORTED, "user-defined stages in a batched call");
   for (int64_t i = 0; i < n; ++i) {
     const int64_t off = desc[5 * i], W = desc[5 * i + 1], H = desc[5 * i + 2], pitch = desc[5 * i + 3];
     if (W < 1 || H < 1 || W > (1 << 20) || H > (1 << 20)) return fail(MRW_ERR_SHAPE, "instance %lld: bad size", (long long)i);
@@ -2265,13 +2498,16 @@ const char *op_name(int k) {
     case OP_MIRROR: return "mirror";
     case OP_BLUR: return "blur5";
     case OP_THRESH: return "threshold3";
+    case OP_USER: return "user";
   }
   return "?";
 }
 
 void ops_json(std::ostringstream &o, const std::vector<ImgStage> &v) {
   o << "[";
-  for (size_t i = 0; i < v.size(); ++i) o << (i ? "," : "") << "\"" << op_name(v[i].kind) << "\"";
+  for (size_t i = 0; i < v.size(); ++i)
+    o << (i ? "," : "") << "\"" << (v[i].kind == OP_USER ? "user:" + v[i].fn->name : std::string(op_name(v[i].kind)))
+      << "\"";
   o << "]";
 }
 
@@ -2293,7 +2529,10 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     for (size_t i = 0; i < gs.size(); ++i) {
       const Group &g = gs[i];
       o << (i ? "," : "") << "{";
-      if (g.use_stencil) {
+      if (g.user) {
+        o << "\"kernel\":\"user_chain\",\"ops\":";
+        ops_json(o, g.pre);
+      } else if (g.use_stencil) {
         StencilArgs sa{};
         fill_stencil_ops(g, sa);
         const StencilShape s = stencil_shape(c, sa);
@@ -2372,7 +2611,7 @@ mrw_status features_of(const Program &p, const mrw_buffer *args, int nargs, floa
   int nn = 0, npw = 0, nm = 0, nb = 0;
   for (const ImgStage &s : p.img) {
     nn += s.kind == OP_NOISE;
-    npw += s.kind == OP_SOLARISE || s.kind == OP_THRESH;
+    npw += s.kind == OP_SOLARISE || s.kind == OP_THRESH || s.kind == OP_USER;
     nm += s.kind == OP_MIRROR;
     nb += s.kind == OP_BLUR;
   }
@@ -2822,6 +3061,7 @@ mrw_status collect_image_stages(const mrw_node *n, ImgStage *out, int *cnt, int 
   if (depth > 64) return fail(MRW_ERR_UNSUPPORTED, "tree deeper than 64 levels");
   switch (n->kind) {
     case N_STAGE: {
+      if (n->user) return fail(MRW_ERR_UNSUPPORTED, "user-defined stages in the allocation-free batched call");
       const int ok = op_kind_of(n->stage);
       if (ok < 0) return fail(MRW_ERR_UNSUPPORTED, "the allocation-free batched call runs image stages only");
       if (*cnt >= cap) return fail(MRW_ERR_UNSUPPORTED, "more than %d image stages", cap);

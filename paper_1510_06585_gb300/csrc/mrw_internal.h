@@ -6,12 +6,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mrw {
 
 // ------------------------------------------------------------------------------------------
 // Image stages, as seen by the fused kernels
 // ------------------------------------------------------------------------------------------
-enum OpKind : int32_t { OP_NOISE = 0, OP_SOLARISE = 1, OP_MIRROR = 2, OP_BLUR = 3, OP_THRESH = 4 };
+// OP_USER (a user-defined stage) never reaches the built-in kernels: groups that contain one run
+// on a kernel compiled at run time (jit.cpp).
+enum OpKind : int32_t { OP_NOISE = 0, OP_SOLARISE = 1, OP_MIRROR = 2, OP_BLUR = 3, OP_THRESH = 4, OP_USER = 5 };
 enum RedKind : int32_t { RED_NONE = 0, RED_COUNT3 = 1, RED_SUM = 2 };
 
 constexpr int kMaxChainOps = 16;     // pointwise ops fused into one kernel
@@ -231,6 +235,34 @@ cudaError_t launch_compare_copy(const uint8_t *b, uint8_t *a, int64_t rows, int3
 cudaError_t launch_while_control(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, cudaStream_t s);
 // words[0] (changed flag) and words[1] (body status word) are zeroed with the counter.
 cudaError_t launch_while_init(LoopCtrl *ctrl, unsigned int *words, unsigned long long max_iters, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Pointwise groups with user-defined stages, compiled at run time (jit.cpp)
+// ------------------------------------------------------------------------------------------
+// Parameter block of the generated kernel, passed by value; the generated source declares the
+// same struct from the same field list (kUserArgsFields), so both sides agree on its layout.
+constexpr int kUserParams = 8;  // 32-bit parameters of each op of the group
+#define MRW_USER_ARGS_FIELDS                                                                        \
+  const unsigned char *in;                                                                          \
+  unsigned char *out;                                                                               \
+  long long in_pitch, out_pitch, rows, row0;                                                        \
+  int W;                                                                                            \
+  unsigned int p[16][8];
+struct UserChainArgs {
+  MRW_USER_ARGS_FIELDS
+};
+#define MRW_STRINGIFY_(...) #__VA_ARGS__
+#define MRW_STRINGIFY(...) MRW_STRINGIFY_(__VA_ARGS__)
+constexpr const char *kUserArgsFields = MRW_STRINGIFY(MRW_USER_ARGS_FIELDS);
+static_assert(kMaxChainOps == 16 && kUserParams == 8, "the field list spells out p[16][8]");
+
+// Compiles `src` with NVRTC for sm_<arch>a without loading it; false with the compiler's message in
+// *err if NVRTC is missing or the source does not compile.
+bool jit_check(const std::string &src, int arch, std::string *err);
+// The kernel `entry` of `src` compiled for sm_<arch>a and loaded on `device` (cached per source and
+// device for the life of the process); false with a message in *err.
+bool jit_kernel(const std::string &src, const char *entry, int device, int arch, cudaKernel_t *kernel,
+                std::string *err);
 
 // ------------------------------------------------------------------------------------------
 // Cost-model MLP (bf16 weights, fp32 accumulation)

@@ -63,6 +63,8 @@ _SIGS = {
     "mrw_last_error": (ctypes.c_char_p, []),
     "mrw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mrw_stage": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(mrw_stage_params), ctypes.POINTER(_P)]),
+    "mrw_stage_user": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(_P)]),
     "mrw_pipeline_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
     "mrw_pipeline_add_stage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(mrw_stage_params)]),
     "mrw_pipeline_add_node": (ctypes.c_int, [_P, _P]),
@@ -250,6 +252,18 @@ def stage(kind, **kw) -> Node:
         kind = STAGE_BY_NAME[kind]
     out = ctypes.c_void_p()
     check(lib.mrw_stage(kind, ctypes.byref(params(**kw)), ctypes.byref(out)), "mrw_stage")
+    return Node(out)
+
+
+def user_stage(name: str, source: str, params=None) -> Node:
+    """mrw_stage_user: a u8 stage whose per-pixel device function `name` is defined by the CUDA C
+    `source`; `params` are its (at most 8) unsigned 32-bit parameters."""
+    vals = [int(v) & 0xFFFFFFFF for v in (params or [])]
+    if len(vals) > 8:
+        raise ValueError("a user stage takes at most 8 parameters")
+    arr = (ctypes.c_uint32 * 8)(*(vals + [0] * (8 - len(vals))))
+    out = ctypes.c_void_p()
+    check(load().mrw_stage_user(name.encode(), source.encode(), arr, ctypes.byref(out)), "mrw_stage_user")
     return Node(out)
 
 
