@@ -1,8 +1,8 @@
 """Oracle for the FFT pipeline stages — test infrastructure only (see ``oracle/__init__``).
 
-Section 4 of the paper (FFT benchmark): a set of fast Fourier transforms, adapted from the SHOC
-suite, each pipelined with its inversion; the elementary partitioning unit is one FFT of 512 KB,
-i.e. 65,536 single-precision complex values. The transforms are the discrete Fourier transform and
+Section 4 of the paper (FFT benchmark): SHOC-derived fast Fourier transforms, each followed in a
+Pipeline by the inverse transform; one transform of 512 KB (65,536 single-precision complex values)
+is the unit the data is partitioned by. The transforms are the discrete Fourier transform and
 its inverse, applied to every row of an (nfft, N) complex array:
 
 * fft  : X[k] = sum_n x[n] exp(-2 pi i n k / N)            (forward, not normalised)
