@@ -152,6 +152,21 @@ __device__ __forceinline__ void pass2(float2 *d, int line, int t, float2 (&v)[16
   for (int k2 = 0; k2 < 16; ++k2) d[line_idx<AB>(line, t + 16 * k2)] = fin(k2, v[dft16_slot(k2)]);
 }
 
+// Pass 2 from values already in place: the 16-point DFT over row t of the 16 x 16 line matrix,
+// X[t + 16 k2] scaled and written to position t + 16 k2.
+template <int S, bool AB>
+__device__ __forceinline__ void pass2_in_place(float2 *d, int line, int t, float scale) {
+  float2 v[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) v[n2] = d[line_idx<AB>(line, 16 * t + n2)];
+  dft16<S>(v);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const float2 x = v[dft16_slot(k2)];
+    d[line_idx<AB>(line, t + 16 * k2)] = make_float2(x.x * scale, x.y * scale);
+  }
+}
+
 // One transform (sign S) of this CTA's quarter: column transforms (input layout AB or BA), the
 // exchange, row transforms into layout BA. Every thread of every CTA of the cluster calls it.
 template <int S, bool AB>
@@ -173,25 +188,54 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
     });
   }
   cluster.sync();  // every quarter's column transforms are done
-  // pull the values of this CTA's rows k1 = 64 rank + line for b = t + 16 m from their owners
   constexpr int kRounds = kCols / (kThreads / 16);
-  float2 v[kRounds][16];
+  if constexpr (AB) {
+    // pull the values of this CTA's rows k1 = 64 rank + line for b = t + 16 m from their owners;
+    // in layout AB a half warp's 16 values of one line are contiguous in the owner's memory
+    float2 v[kRounds][16];
 #pragma unroll
-  for (int rd = 0; rd < kRounds; ++rd) {
-    const int k1 = kCols * rank + g + rd * (kThreads / 16);
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int k1 = kCols * rank + g + rd * (kThreads / 16);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int b = t + 16 * m;  // owned by rank b / 64 = m / 4
-      const int i = AB ? ab(k1, b & 63) : ba(b & 63, k1);
-      v[rd][m] = ld_cluster(cluster_addr(d + i, (uint32_t)(m >> 2)));
+      for (int m = 0; m < 16; ++m) {
+        const int b = t + 16 * m;  // owned by rank b / 64 = m / 4
+        v[rd][m] = ld_cluster(cluster_addr(d + ab(k1, b & 63), (uint32_t)(m >> 2)));
+      }
+      pass1<S>(v[rd], t, sm.tw);
     }
-    pass1<S>(v[rd], t, sm.tw);
-  }
-  cluster.sync();  // every pull is done: the quarters may be overwritten
+    cluster.sync();  // every pull is done: the quarters may be overwritten
 #pragma unroll
-  for (int rd = 0; rd < kRounds; ++rd) {
-    const int line = g + rd * (kThreads / 16);
-    pass2<S, false>(d, line, t, v[rd], [&](int, float2 x) { return make_float2(x.x * scale, x.y * scale); });
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int line = g + rd * (kThreads / 16);
+      pass2<S, false>(d, line, t, v[rd], [&](int, float2 x) { return make_float2(x.x * scale, x.y * scale); });
+    }
+  } else {
+    // In layout BA one value b of 32 consecutive lines is contiguous: a warp pulls for 32 lines at
+    // one position tq (one line per lane), so each pull reads whole 32-byte sectors of the owner's
+    // memory; the pass-1 results then go to this CTA's rows and pass 2 reads them back with the
+    // usual mapping (half a warp per line) after a barrier.
+    const int tq = tid >> 5, gq = tid & 31;
+    float2 v[kRounds][16];
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int k1 = kCols * rank + gq + rd * 32;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int b = tq + 16 * m;  // owned by rank b / 64 = m / 4
+        v[rd][m] = ld_cluster(cluster_addr(d + ba(b & 63, k1), (uint32_t)(m >> 2)));
+      }
+      pass1<S>(v[rd], tq, sm.tw);
+    }
+    cluster.sync();  // every pull is done: the quarters may be overwritten
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int line = gq + rd * 32;
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) d[ba(line, 16 * k1 + tq)] = v[rd][dft16_slot(k1)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) pass2_in_place<S, false>(d, g + rd * (kThreads / 16), t, scale);
   }
   __syncthreads();
 }
@@ -237,13 +281,23 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     // this CTA's columns of row f: element (a, j) = x[256 a + 64 rank + j], layout AB; two values
     // per 16-byte load
     const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kCols * rank);
-#pragma unroll 4
-    for (int e = tid; e < kN / 8; e += kThreads) {
-      int r, j;
-      fft_io_slot(e, &r, &j);
-      const float4 q = __ldcs(src + 128 * r + (j >> 1));
-      sm.d[ab(r, j)] = make_float2(q.x, q.y);
-      sm.d[ab(r, j + 1)] = make_float2(q.z, q.w);
+    {
+      // all of the thread's 16 loads in flight before the first store to shared memory
+      constexpr int kLoads = kN / 8 / kThreads;
+      float4 q[kLoads];
+#pragma unroll
+      for (int i = 0; i < kLoads; ++i) {
+        int r, j;
+        fft_io_slot(tid + i * kThreads, &r, &j);
+        q[i] = __ldcs(src + 128 * r + (j >> 1));
+      }
+#pragma unroll
+      for (int i = 0; i < kLoads; ++i) {
+        int r, j;
+        fft_io_slot(tid + i * kThreads, &r, &j);
+        sm.d[ab(r, j)] = make_float2(q[i].x, q[i].y);
+        sm.d[ab(r, j + 1)] = make_float2(q[i].z, q[i].w);
+      }
     }
     __syncthreads();
     for (int s = 0; s < a.nsteps; ++s) {
