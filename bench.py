@@ -300,6 +300,25 @@ def run_mrw(args):
     assert np.array_equal(hc.numpy(), hist)
     e2e_value = world * SEG_BYTES * k_e2e / t_e2e / 1e9
 
+    # what the host link carries: the copy engines moving the same bytes both ways at once (the
+    # input to the device on one stream, the device labels back on another), 128 MiB each way
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    dx_, dy_ = sets[0][0], sets[1][1]
+
+    def link_step(i):
+        cur = torch.cuda.current_stream()
+        s_in.wait_stream(cur)
+        s_out.wait_stream(cur)
+        with torch.cuda.stream(s_in):
+            dx_.copy_(hx, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            hy.copy_(dy_, non_blocking=True)
+        cur.wait_stream(s_in)
+        cur.wait_stream(s_out)
+    k_link = max(1, min(K, 20))
+    t_link = time_steps(link_step, k_link, min(W, 3), world, device)
+    link_gbs = world * 2 * 512 ** 3 * k_link / t_link / 1e9
+
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(fused_s * 1e3, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -318,7 +337,10 @@ def run_mrw(args):
                      "frac_of_copy_same_size": round((2 * 512 ** 3 / fused_s) / (2 * 512 ** 3 / t_copy), 4),
                      "note": "achieved = algorithmic bytes / CUDA-event time of the step (one chain-kernel launch per step; the MapReduce finishes inside it)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
-                "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e},
+                "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e,
+                "host_link_copy_gbs": round(link_gbs, 2), "frac_of_host_link": round(e2e_value / link_gbs, 4),
+                "note": "pinned host buffers read and written in place over NVLink-C2C by the fused kernel; "
+                        "host_link_copy_gbs = the copy engines moving the same bytes both ways at once"},
         "gpu_launches": K,
         "host_enqueue_us_per_step": round(host_enqueue_us, 2),
         "clocks": sampler.summary(),
