@@ -586,9 +586,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded 3-component mixture volume)",
-            "config": {"workload": WORKLOAD + " (oracle on a 32-plane sample per step)", "shape": [32, 512, 512]},
+            "config": {"workload": WORKLOAD, "shape": list(SEG_SHAPE)},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "32 of 512 planes (8 MiB) per step, numpy single thread"},
+                             "sample": "each step: Map+MapReduce on 32 of the 512 planes (8 MiB in, 8 MiB of "
+                                       "labels out), numpy single thread; GB/s = bytes of the sample / time"},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
