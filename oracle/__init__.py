@@ -17,7 +17,9 @@ Multi-CPU/Multi-GPU Environments"):
                         configuration-derivation step of Section 3.2);
 * ``oracle.partition``— the partitioning constraints of Section 3.1;
 * ``oracle.fft``      — forward and inverse DFT of every row, stage after
-                        stage (Section 4, FFT pipelined with its inversion).
+                        stage (Section 4, FFT pipelined with its inversion);
+* ``oracle.batch``    — per-instance digests of a whole batch of Filter
+                        Pipeline + blur instances, in a pool of processes.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import or run anything here. The CUDA product path never

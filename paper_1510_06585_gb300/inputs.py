@@ -124,6 +124,11 @@ def batch_descriptors(shapes: np.ndarray, align: int = 256) -> tuple[np.ndarray,
     return desc, off
 
 
+def batch_instance(i: int, w: int, h: int, seed: int = SEED_BATCH) -> np.ndarray:
+    """Pixels of instance i of a batch: (h, w) uint8 from its own PCG64 stream."""
+    return _rng(seed * 1_000_000 + i).integers(0, 256, size=(h, w), dtype=np.uint8)
+
+
 def batch_arena(desc: np.ndarray, nbytes: int, seed: int = SEED_BATCH, out: np.ndarray | None = None,
                 indices=None) -> np.ndarray:
     """Fill a uint8 arena with each instance's pixels (padding bytes are 0)."""
@@ -132,9 +137,8 @@ def batch_arena(desc: np.ndarray, nbytes: int, seed: int = SEED_BATCH, out: np.n
     idx = range(desc.shape[0]) if indices is None else indices
     for i in idx:
         off, w, h, pitch, _ = (int(t) for t in desc[i])
-        img = _rng(seed * 1_000_000 + i).integers(0, 256, size=(h, w), dtype=np.uint8)
         view = out[off:off + h * pitch].reshape(h, pitch)
-        view[:, :w] = img
+        view[:, :w] = batch_instance(i, w, h, seed)
     return out
 
 

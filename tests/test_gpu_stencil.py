@@ -1,11 +1,14 @@
 """GPU parity of the TMA-staged stencil groups (5x5 box blur fused with pointwise prefixes and
 suffixes) and of batched execution, against the CPU oracle: bit-exact."""
+import os
+
 import numpy as np
 import pytest
 import torch
 
 from gpu_util import build_image_tree, oracle_tree, run_image
 from oracle import image as O
+from oracle import batch as OB
 from oracle import skeleton as S
 from paper_1510_06585_gb300 import inputs
 from paper_1510_06585_gb300 import mrw as M
@@ -135,6 +138,12 @@ def test_batched_4096_log_uniform_full_size():
     idx = set(rng.choice(4096, size=40, replace=False).tolist())
     idx |= {int(np.argmin(shapes.prod(axis=1))), int(np.argmax(shapes.prod(axis=1))), 0, 4095}
     _check_instances(out, arena, desc, sorted(idx))
+    # every instance: the oracle's output digests (computed by a pool of spawned processes from the
+    # seeded inputs) against the digests of the executor's output
+    want = OB.batch_digests(desc, processes=max(1, min(16, os.cpu_count() or 1)))
+    got = [OB.digest(inputs.instance_view(out, desc[i])) for i in range(len(desc))]
+    bad = [i for i in range(len(desc)) if got[i] != want[i]]
+    assert not bad, (len(bad), bad[:10])
     # a second launch of the cached graph gives the same bytes
     y2 = torch.zeros_like(x)
     M.execute_batched(tree, x, y2, desc).wait(120000)
