@@ -112,6 +112,10 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
                : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
   return r;
 }
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) from global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
   float2 v;
   asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
@@ -310,6 +314,10 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
         else transform<-1, false>(sm, cluster, rank, scale);
       }
     }
+    // the cluster's next row: its 256 segments of this CTA's 64 columns (512 bytes each) into L2
+    // while this row is stored, so that its loads are served from L2
+    if (f + ncl < a.nfft)
+      for (int r = tid; r < 256; r += kThreads) prefetch_l2(a.in + (f + ncl) * kN + 256 * r + kCols * rank, 512u);
     // element (j, a) of layout BA is y[256 a + 64 rank + j]; two values per 16-byte store
     float4 *dst = reinterpret_cast<float4 *>(a.out + f * kN + kCols * rank);
 #pragma unroll 4

@@ -24,6 +24,21 @@ def test_filter_pipeline_1024_fused_and_unfused():
         assert np.array_equal(got, want)
 
 
+def test_filter_pipeline_8192_every_candidate_config():
+    # the roofline-sweep size: every launch shape the tuner may pick (unroll 1..8, persistent and
+    # blocked row orders, prefetching of the next rows) gives the oracle's bytes on 67 M pixels
+    img = inputs.filter_image(8192, 8192)
+    want = O.filter_pipeline(img, inputs.SEED_NOISE)
+    tree = build_image_tree(FILTER, {0: inputs.SEED_NOISE})
+    x, y = to_device(img), empty_like_device(img)
+    cfgs = M.tune_candidates(tree, [x, y])
+    assert len(cfgs) == 16
+    for c in cfgs:
+        y.zero_()
+        M.execute(tree, [x, y], c).wait(60000)
+        assert np.array_equal(y.cpu().numpy(), want), c.as_tuple()
+
+
 def test_filter_pipeline_odd_widths_and_8x8_brute_force():
     tree = build_image_tree(FILTER, {0: 2})
     for (h, w) in [(8, 8), (1, 1), (3, 7)] + [(5, k) for k in range(1, 34)] + [(7, 1000), (2, 1023), (3, 4097)]:
