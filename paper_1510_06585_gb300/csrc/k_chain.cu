@@ -148,12 +148,14 @@ __device__ __forceinline__ void apply_chain(const ChainArgs &a, uint32_t (*w)[4]
 
 __device__ __forceinline__ uint32_t byte_sum(uint32_t v) { return __dp4a(v, 0x01010101u, 0u); }
 
-// CTAs per SM the registers of a variant are budgeted for (at most 64 registers for 4, 80 for 3,
-// 128 for 2). Chains with noise keep 16 column hashes per noise op and the next rows' loads in
-// registers and are ALU-bound, so their budget follows the unroll depth; chains without noise
-// keep the compiler's own choice (0: no minimum).
+// CTAs per SM the registers of a variant are budgeted for (at most 48 registers for 5, 64 for 4,
+// 80 for 3, 128 for 2). Chains with noise keep 16 column hashes per noise op and the next rows'
+// loads in registers and are ALU-bound, so their budget follows the unroll depth. Chains without
+// noise are HBM-bound: at unroll 4 they fit 48 registers, which lets 5 CTAs of 256 threads (a
+// quarter more loads in flight than 4) share an SM; the other depths keep the compiler's choice
+// (0: no minimum).
 constexpr int chain_min_blocks(int nn, int u) {
-  return nn == 0 ? 0 : (nn == 1 ? (u == 1 ? 4 : (u == 2 ? 3 : (u == 4 ? 2 : 1))) : (u <= 2 ? 2 : 1));
+  return nn == 0 ? (u == 4 ? 5 : 0) : (nn == 1 ? (u == 1 ? 4 : (u == 2 ? 3 : (u == 4 ? 2 : 1))) : (u <= 2 ? 2 : 1));
 }
 
 template <int NN, bool MIR, int U>
