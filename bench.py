@@ -187,10 +187,13 @@ def time_steps(fn, steps, warmup, world, device, sampler=None):
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device)
 
 
-def tune_candidates(M, tree, args, reps=5):
-    """Time the 16 candidate configurations; return (best fused, best kernel-per-stage, summary)."""
+def tune_candidates(M, tree, args, reps=15, passes=2):
+    """Time the 16 candidate configurations; return (best fused, best kernel-per-stage, summary).
+    Each pass times every candidate (median of `reps` runs); a candidate keeps its best pass, so
+    that a drift of the clock during one pass does not decide between candidates a few per cent
+    apart."""
     cfgs = M.tune_candidates(tree, args)
-    t = M.tune_measure(tree, args, cfgs, reps=reps)
+    t = np.min(np.stack([np.asarray(M.tune_measure(tree, args, cfgs, reps=reps)) for _ in range(passes)]), axis=0)
     fused = [i for i in range(len(cfgs)) if cfgs[i].fusion == M.MRW_FUSE_ALL and t[i] > 0]
     unfused = [i for i in range(len(cfgs)) if cfgs[i].fusion == M.MRW_FUSE_NONE and t[i] > 0]
     bf = min(fused, key=lambda i: t[i])
