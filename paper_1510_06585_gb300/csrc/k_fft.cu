@@ -8,20 +8,22 @@
 // transforms along the rows (over b). Reading the result Y[k1 + 256 k2] as a matrix U[k2][k1]
 // gives the same shape again, so transforms chain.
 //
-// One cluster of 4 CTAs per row: CTA r owns the 64 columns b in [64r, 64r + 64) of V, and after
-// the row transforms the rows k1 in [64r, 64r + 64) of the result - which are the columns
-// [64r, 64r + 64) of U. Column transforms are local to a CTA; between the two halves of a transform
-// each thread pulls the 32 values its row transforms need from the owning CTAs' shared memory
-// (distributed shared memory), between two cluster barriers. A following transform starts from
-// shared memory; only the first reads and the last writes HBM.
+// One cluster of C = kFftCluster CTAs per row (8; 4 is also supported): CTA r owns the c = 256 / C
+// columns b in [c r, c r + c) of V, and after the row transforms the rows k1 in [c r, c r + c) of
+// the result - which are the columns [c r, c r + c) of U. Column transforms are local to a CTA;
+// between the two halves of a transform each thread pulls the 32 values its row transforms need
+// from the owning CTAs' shared memory (distributed shared memory), between two cluster barriers. A
+// following transform starts from shared memory; only the first reads and the last writes HBM.
+// With 8 CTAs of 256 threads (64 KB of the row and 32 K registers each) two CTAs share an SM, so
+// one cluster's loads, stores and barriers overlap another's arithmetic.
 //
 // 256-point transforms: half a warp per line, radix 16 x 16. Thread t reads positions t + 16 m,
 // does a 16-point DFT (radix 4 x 4 in registers), multiplies by W_256^(t k1), transposes through
 // shared memory inside its line, does a second 16-point DFT and writes position t + 16 k2.
 //
 // Shared-memory layouts (8-byte elements, bank-conflict-free for every access pattern used here):
-//   AB (the first transform's input, element (a, j), j = b - 64 r):
-//       a * 64 + (j ^ ((a ^ (a >> 4)) & 15))
+//   AB (the first transform's input, element (a, j), j = b - c r):
+//       a * c + (j ^ ((a ^ (a >> 4)) & 15))
 //   BA (everything after the first exchange, element (j, a)):
 //       j * 256 + ((a & 0xF0) | ((a ^ (a >> 4) ^ j) & 15))
 #include <cooperative_groups.h>
@@ -34,16 +36,21 @@ namespace mrw {
 namespace {
 
 constexpr int kN = kFftN;          // 65536
-constexpr int kCols = 64;          // columns per CTA
-constexpr int kThreads = 512;      // 16 warps: 32 lines at a time, half a warp each
+constexpr int kCols = 256 / kFftCluster;                // columns per CTA (64 or 32)
+constexpr int kThreads = kFftCluster == 4 ? 512 : 256;  // half a warp per line, kLines lines at a time
+constexpr int kLines = kThreads / 16;                   // lines a CTA transforms at once
+constexpr int kUnits = kN / kFftCluster / 2;            // 16-byte units of a CTA's part of a row
+constexpr int kMinBlocks = kFftCluster == 4 ? 1 : 2;    // CTAs per SM the registers are budgeted for
+static_assert(kFftCluster == 4 || kFftCluster == 8, "clusters of 4 or 8 CTAs");
+static_assert(kCols % kLines == 0 && kUnits % kThreads == 0, "whole rounds");
 constexpr float kC8 = 0.92387953251128675613f;  // cos(pi / 8)
 constexpr float kS8 = 0.38268343236508977173f;  // sin(pi / 8)
 constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1 / 2)
 
 struct FftSmem {
-  float2 d[kN / 4];      // this CTA's quarter of the row (128 KB)
+  float2 d[kN / kFftCluster];  // this CTA's part of the row (128 or 64 KB)
   float2 tw[16][16];     // W_256^(t k), stored at [k][t] (forward sign)
-  float2 tlo[kCols][16]; // W_N^(b l),      b = 64 r + j, l < 16
+  float2 tlo[kCols][16]; // W_N^(b l),      b = kCols r + j, l < 16
   float2 thi[kCols][16]; // W_N^(16 b h),   h < 16
 };
 
@@ -171,7 +178,7 @@ __device__ __forceinline__ void pass2_in_place(float2 *d, int line, int t, float
   }
 }
 
-// One transform (sign S) of this CTA's quarter: column transforms (input layout AB or BA), the
+// One transform (sign S) of this CTA's part: column transforms (input layout AB or BA), the
 // exchange, row transforms into layout BA. Every thread of every CTA of the cluster calls it.
 template <int S, bool AB>
 __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, float scale) {
@@ -191,10 +198,10 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
       return cmul(x, cmul(lo, conj_if(sm.thi[line][k2], S < 0)));
     });
   }
-  cluster.sync();  // every quarter's column transforms are done
+  cluster.sync();  // every part's column transforms are done
   constexpr int kRounds = kCols / (kThreads / 16);
   if constexpr (AB) {
-    // pull the values of this CTA's rows k1 = 64 rank + line for b = t + 16 m from their owners;
+    // pull the values of this CTA's rows k1 = kCols rank + line for b = t + 16 m from their owners;
     // in layout AB a half warp's 16 values of one line are contiguous in the owner's memory
     float2 v[kRounds][16];
 #pragma unroll
@@ -202,12 +209,12 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
       const int k1 = kCols * rank + g + rd * (kThreads / 16);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int b = t + 16 * m;  // owned by rank b / 64 = m / 4
-        v[rd][m] = ld_cluster(cluster_addr(d + ab(k1, b & 63), (uint32_t)(m >> 2)));
+        const int b = t + 16 * m;  // owned by rank b / kCols = m / (kCols / 16)
+        v[rd][m] = ld_cluster(cluster_addr(d + ab(k1, b & (kCols - 1)), (uint32_t)(m / (kCols / 16))));
       }
       pass1<S>(v[rd], t, sm.tw);
     }
-    cluster.sync();  // every pull is done: the quarters may be overwritten
+    cluster.sync();  // every pull is done: the parts may be overwritten
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) {
       const int line = g + rd * (kThreads / 16);
@@ -218,22 +225,22 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
     // one position tq (one line per lane), so each pull reads whole 32-byte sectors of the owner's
     // memory; the pass-1 results then go to this CTA's rows and pass 2 reads them back with the
     // usual mapping (half a warp per line) after a barrier.
-    const int tq = tid >> 5, gq = tid & 31;
+    const int tq = tid / kLines, gq = tid % kLines;
     float2 v[kRounds][16];
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) {
-      const int k1 = kCols * rank + gq + rd * 32;
+      const int k1 = kCols * rank + gq + rd * kLines;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int b = tq + 16 * m;  // owned by rank b / 64 = m / 4
-        v[rd][m] = ld_cluster(cluster_addr(d + ba(b & 63, k1), (uint32_t)(m >> 2)));
+        v[rd][m] = ld_cluster(cluster_addr(d + ba(b & (kCols - 1), k1), (uint32_t)(m / (kCols / 16))));
       }
       pass1<S>(v[rd], tq, sm.tw);
     }
-    cluster.sync();  // every pull is done: the quarters may be overwritten
+    cluster.sync();  // every pull is done: the parts may be overwritten
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) {
-      const int line = gq + rd * 32;
+      const int line = gq + rd * kLines;
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) d[ba(line, 16 * k1 + tq)] = v[rd][dft16_slot(k1)];
     }
@@ -244,17 +251,23 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
   __syncthreads();
 }
 
-// Row r and first column j of the 16-byte unit e (0 .. 8191) of a CTA's part, for the global loads
-// and stores: a warp covers two rows (r even and r + 1) and half of their 64 columns, 8 lanes per
-// 128-byte segment; each half warp then touches 16 distinct bank pairs in both layouts (the
-// swizzles of rows r and r + 1 differ in their lowest bit).
+// Row r and first column j of the 16-byte unit e (0 .. kUnits - 1) of a CTA's part, for the global
+// loads and stores: a warp covers two rows (r even and r + 1) and 32 of their columns (all 32 of
+// them in clusters of 8, one half of 64 in clusters of 4), 8 lanes per 128-byte segment; each half
+// warp then touches 16 distinct bank pairs in both layouts (the swizzles of rows r and r + 1 differ
+// in their lowest bit).
 __device__ __forceinline__ void fft_io_slot(int e, int *r, int *j) {
   const int ws = e >> 5, lane = e & 31;
-  *r = 2 * (ws >> 1) + ((lane >> 3) & 1);
-  *j = 32 * (ws & 1) + 2 * ((lane & 7) + 8 * (lane >> 4));
+  if constexpr (kCols == 64) {
+    *r = 2 * (ws >> 1) + ((lane >> 3) & 1);
+    *j = 32 * (ws & 1) + 2 * ((lane & 7) + 8 * (lane >> 4));
+  } else {
+    *r = 2 * ws + ((lane >> 3) & 1);
+    *j = 2 * ((lane & 7) + 8 * (lane >> 4));
+  }
 }
 
-__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, kMinBlocks)
     fft_cluster_kernel(const __grid_constant__ FftArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   FftSmem &sm = *reinterpret_cast<FftSmem *>(smem_raw);
@@ -282,12 +295,12 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
   __syncthreads();
 
   for (int64_t f = cl; f < a.nfft; f += ncl) {
-    // this CTA's columns of row f: element (a, j) = x[256 a + 64 rank + j], layout AB; two values
+    // this CTA's columns of row f: element (a, j) = x[256 a + kCols rank + j], layout AB; two values
     // per 16-byte load
     const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kCols * rank);
     {
       // all of the thread's 16 loads in flight before the first store to shared memory
-      constexpr int kLoads = kN / 8 / kThreads;
+      constexpr int kLoads = kUnits / kThreads;
       float4 q[kLoads];
 #pragma unroll
       for (int i = 0; i < kLoads; ++i) {
@@ -317,11 +330,12 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     // the cluster's next row: its 256 segments of this CTA's 64 columns (512 bytes each) into L2
     // while this row is stored, so that its loads are served from L2
     if (f + ncl < a.nfft)
-      for (int r = tid; r < 256; r += kThreads) prefetch_l2(a.in + (f + ncl) * kN + 256 * r + kCols * rank, 512u);
-    // element (j, a) of layout BA is y[256 a + 64 rank + j]; two values per 16-byte store
+      for (int r = tid; r < 256; r += kThreads)
+        prefetch_l2(a.in + (f + ncl) * kN + 256 * r + kCols * rank, (uint32_t)(8 * kCols));
+    // element (j, a) of layout BA is y[256 a + kCols rank + j]; two values per 16-byte store
     float4 *dst = reinterpret_cast<float4 *>(a.out + f * kN + kCols * rank);
 #pragma unroll 4
-    for (int e = tid; e < kN / 8; e += kThreads) {
+    for (int e = tid; e < kUnits; e += kThreads) {
       int r, j;
       fft_io_slot(e, &r, &j);
       const float2 lo = sm.d[ba(j, r)], hi = sm.d[ba(j + 1, r)];

@@ -184,7 +184,7 @@ cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t
 // FFT stages: rows of kFftN complex float32 values, a cluster of kFftCluster CTAs per row
 // ------------------------------------------------------------------------------------------
 constexpr int kFftN = 65536;
-constexpr int kFftCluster = 4;
+constexpr int kFftCluster = 8;
 constexpr int kFftMaxSteps = 8;
 struct FftArgs {
   const float2 *in;              // nfft rows of kFftN values (16-byte aligned, dense)
