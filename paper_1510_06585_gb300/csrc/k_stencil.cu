@@ -698,12 +698,13 @@ __global__ void __launch_bounds__(kRowsBlock, MINB) stencil_rows_kernel(const __
       uint32_t h02[kRowsGroup], h13[kRowsGroup];
 #pragma unroll
       for (int j = 0; j < kRowsGroup; ++j) {
-        const uint32_t nb = __shfl_down_sync(0xFFFFFFFFu, q[j], 1);
-        // horizontal 5-sums of output columns 0..3 (Q bytes k .. k + 4 of q:nb), packed as
-        // (0, 2) and (1, 3) in 16-bit lanes
+        // horizontal 5-sums of output columns 0..3 (Q bytes k .. k + 4 of this lane's quad and
+        // the next lane's), packed as (0, 2) and (1, 3) in 16-bit lanes; the next lane's even
+        // bytes E2 and pair sums A2 come from it by shuffle, already unpacked
         const uint32_t E = __byte_perm(q[j], 0, 0x4240), O = __byte_perm(q[j], 0, 0x4341);
-        const uint32_t E2 = __byte_perm(nb, 0, 0x4240), O2 = __byte_perm(nb, 0, 0x4341);
-        const uint32_t A = E + O, A2 = E2 + O2, P = __byte_perm(A, A2, 0x5432);
+        const uint32_t A = E + O;
+        const uint32_t E2 = __shfl_down_sync(0xFFFFFFFFu, E, 1), A2 = __shfl_down_sync(0xFFFFFFFFu, A, 1);
+        const uint32_t P = __byte_perm(A, A2, 0x5432);
         h02[j] = A + P + E2;
         h13[j] = O + P + A2;
       }
