@@ -292,13 +292,23 @@ def run_mrw(args):
     hc = torch.zeros(3, dtype=torch.int64).pin_memory()
     hbuf = M.buffers(hx, hy, hc)
 
-    def e2e_step(i):
-        fut = ctypes.c_void_p()
-        M.check(lib.mrw_execute(tree.h, hbuf, 3, ctypes.byref(fused_cfg), stream, ctypes.byref(fut)), "execute")
-        pending.append(fut)
+    def e2e_with(cfg):
+        def e2e_step(i):
+            fut = ctypes.c_void_p()
+            M.check(lib.mrw_execute(tree.h, hbuf, 3, ctypes.byref(cfg), stream, ctypes.byref(fut)), "execute")
+            pending.append(fut)
+        return e2e_step
 
+    # the launch shape that suits HBM need not suit the host link: pick the end-to-end run's own
+    # among the fused candidates, by a few timed steps each on these host buffers
+    e2e_cands = [c for c in M.tune_candidates(tree, list(sets[0])) if c.fusion == M.MRW_FUSE_ALL]
+    e2e_t = []
+    for c in e2e_cands:
+        e2e_t.append(time_steps(e2e_with(c), 4, 1, world, device))
+        drain()
+    e2e_cfg = e2e_cands[int(np.argmin(e2e_t))]
     k_e2e = max(1, min(K, 50))
-    t_e2e = time_steps(e2e_step, k_e2e, min(W, 3), world, device)
+    t_e2e = time_steps(e2e_with(e2e_cfg), k_e2e, min(W, 3), world, device)
     drain()
     assert np.array_equal(hc.numpy(), hist)
     e2e_value = world * SEG_BYTES * k_e2e / t_e2e / 1e9
@@ -342,6 +352,7 @@ def run_mrw(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
                 "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e,
                 "host_link_copy_gbs": round(link_gbs, 2), "frac_of_host_link": round(e2e_value / link_gbs, 4),
+                "cfg": list(e2e_cfg.as_tuple()),
                 "note": "pinned host buffers read and written in place over NVLink-C2C by the fused kernel; "
                         "host_link_copy_gbs = the copy engines moving the same bytes both ways at once"},
         "gpu_launches": K,

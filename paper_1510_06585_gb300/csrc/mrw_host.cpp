@@ -551,7 +551,7 @@ const Shape kShapes[8] = {
     {512, 2, 4, 64, 64, 2},
     {256, 2, 1, 8, 256, 1},
     {128, 16, 2, 16, 64, 4},
-    {256, 1, 8, 64, 128, 2},
+    {128, 16, 8, 64, 128, 2},
     {1024, 1, 4, 32, 256, 4},
 };
 const int kNbodyCps[8] = {1, 1, 1, 2, 2, 2, 4, 4};
