@@ -265,7 +265,13 @@ def run_mrw(args):
 
     # the executor's autotuner picks the launch configuration (all 16 candidates timed on these
     # buffers); the kernel-per-stage baseline gets the best of its own 8 candidates
-    fused_cfg, unfused_cfg, tuning = tune_candidates(M, tree, list(sets[0]))
+    if args.fused_cfg:  # profiling runs: a given fused shape, no tuner launches before it
+        blk, cps, tr, tc, un = (int(v) for v in args.fused_cfg.split(","))
+        fused_cfg = M.config(block=blk, ctas_per_sm=cps, tile_rows=tr, tile_cols=tc, unroll=un)
+        unfused_cfg = M.config(fusion=M.MRW_FUSE_NONE)
+        tuning = {"fused_cfg": list(fused_cfg.as_tuple()), "note": "given with --fused-cfg (no tuning)"}
+    else:
+        fused_cfg, unfused_cfg, tuning = tune_candidates(M, tree, list(sets[0]))
     sampler = ClockSampler(local)
     t_fused = time_steps(step_async(fused_cfg), K, W, world, device, sampler)
     host_enqueue_us = time_steps.host_enqueue_us  # host time to enqueue one step (no GPU wait inside)
@@ -619,6 +625,9 @@ def main():
                     help="comma list of the extra workloads to run (filter, nbody, batched, fft, costmodel)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--filter-sides", default="1024,4096,8192,16384", help="image sides of the Filter Pipeline workload")
+    ap.add_argument("--fused-cfg", default="",
+                    help="block,ctas_per_sm,tile_rows,tile_cols,unroll of the headline's fused launch "
+                         "(profiling runs; default: the autotuner's choice)")
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
                     help="skip the headline timing (profiling runs of one extra workload)")
     args = ap.parse_args()
