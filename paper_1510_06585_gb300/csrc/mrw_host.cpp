@@ -552,7 +552,7 @@ const Shape kShapes[8] = {
     {256, 2, 1, 8, 256, 1},
     {128, 16, 2, 16, 64, 4},
     {128, 16, 8, 64, 128, 2},
-    {1024, 1, 4, 32, 256, 4},
+    {256, 3, 4, 64, 128, 2},
 };
 const int kNbodyCps[8] = {1, 1, 1, 2, 2, 2, 4, 4};
 
