@@ -327,7 +327,7 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
         else transform<-1, false>(sm, cluster, rank, scale);
       }
     }
-    // the cluster's next row: its 256 segments of this CTA's 64 columns (512 bytes each) into L2
+    // the cluster's next row: its 256 segments of this CTA's kCols columns (8 kCols bytes each) into L2
     // while this row is stored, so that its loads are served from L2
     if (f + ncl < a.nfft)
       for (int r = tid; r < 256; r += kThreads)
