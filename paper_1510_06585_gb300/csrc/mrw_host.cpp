@@ -2503,6 +2503,17 @@ const char *op_name(int k) {
   return "?";
 }
 
+const char *pattern_name(int32_t pat) {
+  switch (pat) {
+    case PAT_NONE: return "none";
+    case PAT_NOISE: return "noise";
+    case PAT_SOLARISE: return "solarise";
+    case PAT_NOISE_SOLARISE: return "noise_solarise";
+    case PAT_THRESH: return "threshold3";
+  }
+  return "generic";
+}
+
 void ops_json(std::ostringstream &o, const std::vector<ImgStage> &v) {
   o << "[";
   for (size_t i = 0; i < v.size(); ++i)
@@ -2539,6 +2550,8 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
         const int64_t tx = (geo.W + s.tile_w - 1) / s.tile_w, ty = (geo.H + s.tile_h - 1) / s.tile_h;
         o << "\"kernel\":\"" << (sa.rows_kernel ? "stencil_rows" : "stencil") << "\",\"pre\":";
         ops_json(o, g.pre);
+        uint32_t pt = 0;
+        o << ",\"pre_pattern\":\"" << pattern_name(op_pattern(sa.pre, sa.npre, &pt)) << "\"";
         o << ",\"blur\":" << (g.blur ? "true" : "false") << ",\"suf\":";
         ops_json(o, g.suf);
         o << ",\"tile\":[" << s.tile_h << "," << s.tile_w << "],\"box\":[" << s.box_h << "," << s.box_w
@@ -2550,6 +2563,10 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
                                          g.reduce != RED_NONE);
         o << "\"kernel\":\"chain\",\"ops\":";
         ops_json(o, g.pre);
+        ChainOp ops[kMaxChainOps];
+        fill_ops(g.pre, mirror_parity(g.pre), ops);
+        uint32_t pt = 0;
+        o << ",\"pattern\":\"" << pattern_name(op_pattern(ops, (int)g.pre.size(), &pt)) << "\"";
         o << ",\"reduce_only\":" << (g.reduce_only ? "true" : "false") << ",\"reduce\":" << g.reduce
           << ",\"nu\":16,\"col_vecs\":" << (geo.W + 15) / 16 << ",\"rows_parallel\":" << s.rows_parallel
           << ",\"grid\":" << s.grid << ",\"block\":" << s.block << ",\"unroll\":" << s.unroll

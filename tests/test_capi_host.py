@@ -220,3 +220,37 @@ def test_while_changed_loops_are_planned_and_validated(lib):
         mrw.plan_describe(mrw.loop(mrw.stage("nbody_kdk", eps=1e-3, dt=1e-3), 5, mrw.MRW_LOOP_WHILE_CHANGED),
                           _nbody_args(16))
     assert e.value.status == mrw.MRW_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("names, pattern", [
+    (["noise", "solarise", "mirror"], "noise_solarise"),
+    (["mirror", "noise", "mirror", "solarise"], "noise_solarise"),
+    (["solarise", "noise"], "generic"),
+    (["noise", "noise"], "generic"),
+    (["noise", "solarise", "solarise"], "generic"),
+    (["noise"], "noise"),
+    (["mirror", "solarise"], "solarise"),
+    (["mirror"], "none"),
+    (["mirror", "mirror"], "none"),
+    (["threshold3", "mirror"], "threshold3"),
+    (["solarise", "threshold3"], "generic"),
+])
+def test_op_sequences_the_kernels_run_without_interpretation(lib, names, pattern):
+    """The host classifies each fused group's op list; mirrors move no data and do not count."""
+    pipe = mrw.pipeline(*[mrw.stage(n, seed=3) if n == "noise" else mrw.stage(n) for n in names])
+    g = mrw.plan_describe(pipe, _image_args(64, 256))["groups"]
+    assert len(g) == 1 and g[0]["kernel"] == "chain" and g[0]["pattern"] == pattern
+    u = mrw.plan_describe(pipe, _image_args(64, 256), mrw.config(fusion=mrw.MRW_FUSE_NONE))["groups"]
+    single = {"noise": "noise", "solarise": "solarise", "mirror": "none", "threshold3": "threshold3"}
+    assert [x["pattern"] for x in u] == [single[n] for n in names]
+
+
+def test_blur_prefix_sequences(lib):
+    d = mrw.plan_describe(mrw.pipeline(mrw.stage("noise", seed=2), mrw.stage("solarise"), mrw.stage("mirror"),
+                                       mrw.stage("blur5")), _image_args(300, 333))["groups"]
+    assert [x["kernel"] for x in d] == ["stencil_rows"] and d[0]["pre_pattern"] == "noise_solarise"
+    d = mrw.plan_describe(mrw.pipeline(mrw.stage("blur5")), _image_args(300, 333))["groups"]
+    assert d[0]["pre_pattern"] == "none"
+    d = mrw.plan_describe(mrw.pipeline(mrw.stage("solarise"), mrw.stage("noise", seed=1), mrw.stage("blur5"),
+                                       mrw.stage("solarise")), _image_args(300, 333))["groups"]
+    assert d[0]["kernel"] == "stencil" and d[0]["pre_pattern"] == "generic"
