@@ -238,7 +238,7 @@ void mrw_node_release(mrw_node_t n);
  *     (nfft, 65536) or (65536), dense rows, 16-byte aligned device pointers; y = the stages applied
  *     to every row of x in order; y may
  *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
- *     transforms in one launch (a 4-CTA cluster per row, the data on chip between transforms);
+ *     transforms in one launch (a cluster of 8 CTAs per row, the data on chip between transforms);
  *     FUSE_NONE runs one launch per transform.
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with

@@ -1,5 +1,5 @@
 """GPU parity of the FFT stages (Section 4, FFT pipelined with its inversion) against the FP64
-oracle: rows of 65,536 complex float32 values, one 4-CTA cluster per row.
+oracle: rows of 65,536 complex float32 values, one cluster of 8 CTAs per row.
 
 Tolerance: normwise relative error per row <= 1e-5. A float32 transform of 2^16 points goes
 through 16 radix-2-equivalent levels, each adding a rounding error of a few units of 2^-24 to the
