@@ -298,9 +298,16 @@ struct mrw_future {
 
 namespace {
 
+// Plan generation: advanced by every change that can alter what an execution of the same tree on
+// the same arguments enqueues (a node created, grown or destroyed; the knowledge base or the
+// installed cost model changed). A prepared launch is replayed only while it is unchanged.
+std::atomic<uint64_t> g_plan_gen{1};
+void bump_plan_gen() { g_plan_gen.fetch_add(1, std::memory_order_acq_rel); }
+
 mrw_node *new_node(NodeKind k) {
   mrw_node *n = new (std::nothrow) mrw_node();
   if (n) n->kind = k;
+  bump_plan_gen();
   return n;
 }
 
@@ -309,6 +316,7 @@ void release_node(mrw_node *n) {
   if (n->refs.fetch_sub(1) == 1) {
     for (mrw_node *c : n->kids) release_node(c);
     delete n;
+    bump_plan_gen();
   }
 }
 
@@ -651,6 +659,24 @@ struct Staged {
   View src;
 };
 
+// A single fused chain launch prepared by an execute call: an image tree that plans into one
+// pointwise kernel over device buffers. The next call of the same thread with the same tree,
+// arguments, configuration, stream and device, and no change of the plan generation in between,
+// replays it without planning again (the host cost of a small image is mostly planning and launch).
+struct ChainReplay {
+  bool valid = false;
+  uint64_t gen = 0;
+  const mrw_node *root = nullptr;
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  int32_t nargs = 0;
+  mrw_buffer args[3];
+  bool has_cfg = false;
+  mrw_config cfg{};
+  ChainArgs a{};
+  int n_noise = 0, unroll = 1, grid = 0, block = 0;
+};
+
 struct Launch {  // everything one execute call enqueues
   cudaStream_t stream;
   int device;
@@ -658,6 +684,8 @@ struct Launch {  // everything one execute call enqueues
   std::vector<void *> scratch;  // freed with cudaFreeAsync at the end
   std::vector<Staged> staged;
   std::vector<cudaEvent_t> *events = nullptr;  // ordering events to keep until the work is done
+  ChainReplay *record = nullptr;  // set by execute: where a replayable chain launch is recorded
+  bool recorded = false;
 
   mrw_status alloc(void **p, size_t bytes) {
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, stream);
@@ -920,6 +948,15 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
   if (s.grid > kMaxChainGrid) return fail(MRW_ERR_UNSUPPORTED, "chain grid above %d CTAs", kMaxChainGrid);
   s.apply(a);
   CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+  if (L.record) {
+    ChainReplay &r = *L.record;
+    r.a = a;
+    r.n_noise = count_noise(g.pre);
+    r.unroll = s.unroll;
+    r.grid = s.grid;
+    r.block = s.block;
+    L.recorded = true;
+  }
   return MRW_OK;
 }
 
@@ -1630,8 +1667,16 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
   View vin, vout, vred;
   TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
   const ImgGeom geo = geom_of(args[0], vin);
-  if (p.while_begin >= 0) return enqueue_image_while(L, p, vin, vout, geo, cfg, status, used_status);
+  if (p.while_begin >= 0) {
+    L.record = nullptr;
+    return enqueue_image_while(L, p, vin, vout, geo, cfg, status, used_status);
+  }
   const std::vector<Group> gs = group_stages(p, cfg.fusion == MRW_FUSE_ALL, false);
+  // only a plan of one chain kernel over device buffers is replayable: nothing else is enqueued
+  if (!(gs.size() == 1 && !gs[0].use_stencil && !gs[0].user && !gs[0].reduce_only &&
+        vin.b->memory == MRW_MEM_DEVICE && vout.b->memory == MRW_MEM_DEVICE &&
+        (p.reduce == RED_NONE || vred.b->memory == MRW_MEM_DEVICE)))
+    L.record = nullptr;
   TRY(prepare_user_groups(L, gs));
   const bool one_chain = gs.size() == 1 && !gs[0].use_stencil && !gs[0].user && vin.b->memory == MRW_MEM_HOST &&
                          vout.b->memory == MRW_MEM_HOST;
@@ -1980,6 +2025,7 @@ mrw_config pick_config(const mrw_node *root, const Program &p, const mrw_buffer 
     if (features_of(p, args, nargs, f) == MRW_OK && model_predict(m, f, &best) == MRW_OK && best >= 0) {
       std::lock_guard<std::mutex> lk(g_mu);
       kb()[key] = {cfgs[best], -1.f, 2};
+      bump_plan_gen();
       return cfgs[best];
     }
   }
@@ -2116,6 +2162,7 @@ mrw_status mrw_pipeline_add_node(mrw_node_t pipe, mrw_node_t child) {
   if (contains(child, pipe)) return fail(MRW_ERR_INVALID_ARG, "adding a node to its own subtree");
   child->refs.fetch_add(1);
   pipe->kids.push_back(child);
+  bump_plan_gen();
   return MRW_OK;
 }
 
@@ -2125,6 +2172,7 @@ mrw_status mrw_pipeline_add_stage(mrw_node_t pipe, mrw_stage_kind kind, const mr
   mrw_node_t st;
   TRY(mrw_stage(kind, params, &st));
   pipe->kids.push_back(st);  // the pipeline takes over the creation reference
+  bump_plan_gen();
   return MRW_OK;
 }
 
@@ -2168,11 +2216,53 @@ void mrw_node_release(mrw_node_t n) { release_node(n); }
 }  // extern "C"
 
 namespace {
+thread_local ChainReplay t_replay;  // the last replayable launch of this thread
+
+bool replay_matches(const ChainReplay &r, const mrw_node *root, const mrw_buffer *args, int32_t nargs,
+                    const mrw_config *cfg, cudaStream_t stream, int device) {
+  return r.valid && r.root == root && r.nargs == nargs && r.stream == stream && r.device == device &&
+         r.gen == g_plan_gen.load(std::memory_order_acquire) && r.has_cfg == (cfg != nullptr) &&
+         (!cfg || memcmp(&r.cfg, cfg, sizeof(mrw_config)) == 0) &&
+         memcmp(r.args, args, (size_t)nargs * sizeof(mrw_buffer)) == 0;
+}
+
+mrw_status replay_chain(const ChainReplay &r, bool timed, mrw_future_t *out) {
+  mrw_future *f = new (std::nothrow) mrw_future();
+  if (!f) return fail(MRW_ERR_OOM, "future");
+  f->device = r.device;
+  mrw_status s = take_future_events(f, timed);
+  if (s != MRW_OK) {
+    free_future(f);
+    return s;
+  }
+  if (timed) cudaEventRecord(f->start, r.stream);
+  const cudaError_t e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
+  cudaEventRecord(f->done, r.stream);
+  if (e != cudaSuccess) {
+    const mrw_status st = cuda_fail(e, "chain kernel launch");
+    const std::string msg = t_err;
+    cudaEventSynchronize(f->done);
+    free_future(f);
+    t_err = msg;
+    return st;
+  }
+  *out = f;
+  return MRW_OK;
+}
+
 mrw_status execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg, void *stream,
                    mrw_future_t *out, bool timed) {
   if (!out) return fail(MRW_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
+  const bool replayable = root && nargs >= 2 && nargs <= 3;
+  if (replayable && t_replay.valid) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        replay_matches(t_replay, root, args, nargs, cfg, (cudaStream_t)stream, dev))
+      return replay_chain(t_replay, timed, out);
+  }
+  const uint64_t gen = g_plan_gen.load(std::memory_order_acquire);  // before anything is planned
   Program p;
   TRY(get_program(root, &p));
   TRY(validate_args(p, args, nargs));
@@ -2192,10 +2282,24 @@ mrw_status execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const
   if (timed) cudaEventRecord(f->start, L.stream);
   bool used = false;
   L.events = &f->sync_events;
+  ChainReplay rec;
+  L.record = replayable && p.fam == F_IMAGE ? &rec : nullptr;
   s = enqueue(L, p, args, nargs, c, f->slot.dev, &used);
   f->has_status = used;  // kernels write failures into the mapped host word itself
   L.free_all();
   cudaEventRecord(f->done, L.stream);
+  if (s == MRW_OK && L.record && L.recorded && !used) {
+    rec.valid = true;
+    rec.gen = gen;
+    rec.root = root;
+    rec.device = L.device;
+    rec.stream = L.stream;
+    rec.nargs = nargs;
+    memcpy(rec.args, args, (size_t)nargs * sizeof(mrw_buffer));
+    rec.has_cfg = cfg != nullptr;
+    if (cfg) rec.cfg = *cfg;
+    t_replay = rec;
+  }
   if (s != MRW_OK) {
     // what was enqueued still runs; wait for it so the future's resources can go
     const std::string msg = t_err;
@@ -2858,6 +2962,7 @@ mrw_status mrw_tune(mrw_node_t root, const mrw_buffer *args, int32_t nargs, mrw_
   {
     std::lock_guard<std::mutex> lk(g_mu);
     kb()[key] = {pick, pick_ms, (int)mode};
+    bump_plan_gen();
   }
   if (best) *best = pick;
   if (best_ms) *best_ms = pick_ms;
@@ -2898,12 +3003,14 @@ mrw_status mrw_kb_load(const char *path) {
   }
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto &kv : add) kb()[kv.first] = kv.second;
+  bump_plan_gen();
   return MRW_OK;
 }
 
 mrw_status mrw_kb_clear(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   kb().clear();
+  bump_plan_gen();
   return MRW_OK;
 }
 
@@ -3054,6 +3161,7 @@ mrw_status mrw_model_train(mrw_model_t m, const float *x, const float *t, int64_
 
 mrw_status mrw_tune_set_model(mrw_model_t m, const mrw_config *cfgs, int32_t k) {
   std::lock_guard<std::mutex> lk(g_mu);
+  bump_plan_gen();
   if (!m) {
     installed_model().model = nullptr;
     installed_model().cfgs.clear();
