@@ -242,7 +242,10 @@ void mrw_node_release(mrw_node_t n);
  *     FUSE_NONE runs one launch per transform.
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with
- * mrw_future_release). `cfg` may be NULL (tuned or default configuration). */
+ * mrw_future_release). `cfg` may be NULL (tuned or default configuration). A call that repeats
+ * the calling thread's previous call (same tree, args, cfg, stream and device, and no tree,
+ * knowledge-base or cost-model change in between) reuses that call's prepared launch when the plan
+ * is a single pointwise kernel over device buffers, which skips the host's planning work. */
 mrw_status mrw_execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
                        void *stream, mrw_future_t *out);
 /* As mrw_execute, and the future also records the call's device time for
