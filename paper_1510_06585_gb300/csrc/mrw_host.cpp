@@ -2989,6 +2989,7 @@ mrw_status mrw_kb_load(const char *path) {
   std::string line;
   std::map<std::string, KbRecord> add;
   while (std::getline(f, line)) {
+    while (!line.empty() && (line.back() == '\r' || line.back() == ' ')) line.pop_back();
     if (line.empty()) continue;
     const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 + 1), t3 = line.find('\t', t2 + 1);
     if (t1 == std::string::npos || t2 == std::string::npos || t3 == std::string::npos)
@@ -2997,8 +2998,14 @@ mrw_status mrw_kb_load(const char *path) {
     std::istringstream cs(line.substr(t1 + 1, t2 - t1 - 1));
     cs >> r.cfg.fusion >> r.cfg.block >> r.cfg.ctas_per_sm >> r.cfg.tile_rows >> r.cfg.tile_cols >> r.cfg.unroll;
     if (!cs || check_config(r.cfg) != MRW_OK) return fail(MRW_ERR_INVALID_ARG, "malformed configuration in %s", path);
-    r.ms = std::stof(line.substr(t2 + 1, t3 - t2 - 1));
-    r.source = std::stoi(line.substr(t3 + 1));
+    // strtof / strtol rather than the throwing std::sto*: nothing may throw across the C ABI
+    const std::string ms = line.substr(t2 + 1, t3 - t2 - 1), src = line.substr(t3 + 1);
+    char *e1 = nullptr, *e2 = nullptr;
+    r.ms = strtof(ms.c_str(), &e1);
+    const long so = strtol(src.c_str(), &e2, 10);
+    if (ms.empty() || src.empty() || *e1 != '\0' || *e2 != '\0' || so < INT32_MIN || so > INT32_MAX)
+      return fail(MRW_ERR_INVALID_ARG, "malformed time or source field in %s", path);
+    r.source = (int)so;
     add[line.substr(0, t1)] = r;
   }
   std::lock_guard<std::mutex> lk(g_mu);

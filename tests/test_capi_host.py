@@ -192,8 +192,14 @@ def test_knowledge_base_roundtrip(lib, tmp_path):
     assert lib.mrw_kb_save(str(out).encode()) == 0
     assert out.read_text() == path.read_text()
     bad = tmp_path / "bad.txt"
-    bad.write_text("only-one-field\n")
-    assert lib.mrw_kb_load(str(bad).encode()) == mrw.MRW_ERR_INVALID_ARG
+    for text in ("only-one-field\n", "k\t1 128 4 16 64 2\tfast\t0\n", "k\t1 128 4 16 64 2\t0.5\t1x\n",
+                 "k\t1 128 4 16 64 2\t\t0\n", "k\t1 128 4 16 64 2\t0.5\t99999999999\n", "k\t1 128\t0.5\t0\n"):
+        bad.write_text(text)
+        assert lib.mrw_kb_load(str(bad).encode()) == mrw.MRW_ERR_INVALID_ARG, text
+    assert lib.mrw_kb_size() == 1  # a failed load adds nothing
+    crlf = tmp_path / "crlf.txt"
+    crlf.write_text(path.read_text().replace("\n", "\r\n"))
+    assert lib.mrw_kb_clear() == 0 and lib.mrw_kb_load(str(crlf).encode()) == 0 and lib.mrw_kb_size() == 1
     lib.mrw_kb_clear()
 
 
