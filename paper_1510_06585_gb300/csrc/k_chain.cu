@@ -18,7 +18,9 @@
 // and are folded into 32-bit counters before a lane can overflow.
 //
 // MapReduce (Section 2.1; merging function +, Section 3.4) is fused: per-thread counters, warp
-// reduction with redux.sync, block reduction in shared memory, one 64-bit atomic per block.
+// reduction with redux.sync, block reduction in shared memory, and one fire-and-forget 64-bit add
+// per block and class into a per-stream set of accumulators; a one-CTA finish kernel, launched
+// behind the chain with programmatic dependent launch, sums the sets into the result.
 #include "mrw_internal.h"
 #include "pixel_ops.cuh"
 
@@ -346,54 +348,49 @@ __global__ void __launch_bounds__(256, chain_min_blocks(NN, U)) chain_kernel(con
     red_smem[warp][2] = r2v;
   }
   __syncthreads();
-  __shared__ bool is_last;
+  if (threadIdx.x != 0) return;
   const int nout = a.reduce == RED_COUNT3 ? 3 : 1;
-  if (threadIdx.x == 0) {
-    unsigned long long t[3] = {0, 0, 0};
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) {
-      t[0] += red_smem[i][0];
-      t[1] += red_smem[i][1];
-      t[2] += red_smem[i][2];
-    }
-    // with a workspace: add into accumulator set blockIdx % kChainSlots (left at zero by the
-    // previous launch), and let the last CTA to arrive sum the sets into `red`; without: add into
-    // a zeroed `red`
-    unsigned long long *dst = a.partials ? a.partials + 3 * (blockIdx.x % kChainSlots) : a.red;
-    for (int k = 0; k < nout; ++k)
-      if (t[k]) atomicAdd(dst + k, t[k]);
-    is_last = false;
-    if (a.partials) {
-      // release: this CTA's adds are visible before its ticket; acquire on the last CTA's side.
-      // acq_rel is enough for this pattern; the sequentially consistent __threadfence() would also
-      // wait for the thread's streaming stores of the image.
-      asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
-    }
+  unsigned long long t[3] = {0, 0, 0};
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < nw; ++i) {
+    t[0] += red_smem[i][0];
+    t[1] += red_smem[i][1];
+    t[2] += red_smem[i][2];
   }
-  __syncthreads();
-  if (!is_last) return;  // uniform over the CTA
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  // with a workspace: add into accumulator set blockIdx % kChainSlots (left at zero by the
+  // previous finish), which the finish kernel sums into `red`; without: add into a zeroed `red`.
+  // The result of the add is not used, so the CTA does not wait for it.
+  unsigned long long *dst = a.partials ? a.partials + 3 * (blockIdx.x % kChainSlots) : a.red;
+  for (int k = 0; k < nout; ++k)
+    if (t[k]) atomicAdd(dst + k, t[k]);
+}
+
+// The MapReduce finish: the kChainSlots accumulator sets of the chain launch before it on the
+// stream, summed into `red` and zeroed for the next launch. Launched with programmatic dependent
+// launch: griddepcontrol.wait returns once that launch has completed and its adds are visible.
+__global__ void __launch_bounds__(kChainSlots) chain_finish_kernel(unsigned long long *partials,
+                                                                   unsigned long long *red, int nout) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __shared__ unsigned long long s[kChainSlots / 32][3];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   unsigned long long v[3] = {0, 0, 0};
-  for (int sl = threadIdx.x; sl < kChainSlots; sl += blockDim.x)
-    for (int k = 0; k < nout; ++k) {
-      v[k] += __ldcg(a.partials + 3 * sl + k);
-      a.partials[3 * sl + k] = 0ull;  // clean for the next launch on this workspace
-    }
+  for (int k = 0; k < nout; ++k) {
+    v[k] = __ldcg(partials + 3 * t + k);
+    partials[3 * t + k] = 0ull;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     for (int k = 0; k < 3; ++k) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
   if (lane == 0)
-    for (int k = 0; k < 3; ++k) red_smem[warp][k] = v[k];
+    for (int k = 0; k < 3; ++k) s[warp][k] = v[k];
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int k = 0; k < nout; ++k) {
-    unsigned long long tot = 0;
-    for (int i = 0; i < nw; ++i) tot += red_smem[i][k];
-    a.red[k] = tot;
-  }
-  *a.ticket = 0u;
+  if (t == 0)
+    for (int k = 0; k < nout; ++k) {
+      unsigned long long tot = 0;
+      for (int i = 0; i < kChainSlots / 32; ++i) tot += s[i][k];
+      red[k] = tot;
+    }
 }
 
 template <int NN, bool MIR, int U>
@@ -439,6 +436,28 @@ int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block) {
   return c;
 }
 
+// Programmatic dependent launch for a launch on `s`, unless `s` is being captured into a graph
+// (the graph keeps plain dependencies).
+static int pdl_attrs(cudaStream_t s, cudaLaunchAttribute *attr) {
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+  return cap == cudaStreamCaptureStatusNone ? 1 : 0;
+}
+
+cudaError_t launch_chain_finish(unsigned long long *partials, unsigned long long *red, int nout, cudaStream_t s) {
+  if (!partials || !red || nout < 1 || nout > 3) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kChainSlots);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_attrs(s, attr);
+  return cudaLaunchKernelEx(&cfg, chain_finish_kernel, partials, red, nout);
+}
+
 cudaError_t launch_chain(const ChainArgs &ca, int n_noise, int unroll, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
   ChainArgs a = ca;
@@ -451,12 +470,8 @@ cudaError_t launch_chain(const ChainArgs &ca, int n_noise, int unroll, int grid,
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
   cfg.attrs = attr;
-  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;  // plain edges inside captured graphs
+  cfg.numAttrs = pdl_attrs(s, attr);
   void *args[] = {(void *)&a};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }

@@ -150,11 +150,10 @@ StatusPool &status_pool() {
   return p;
 }
 
-// Workspace of the chain kernel's in-kernel MapReduce finish: one per (device, stream), so launches
-// that may overlap never share a ticket. The ticket starts at 0 and the last CTA resets it.
+// Accumulators of the chain kernel's MapReduce finish: one set per (device, stream), so launches
+// that may overlap never share accumulators. The finish kernel leaves them at zero.
 struct ChainWs {
   unsigned long long *partials = nullptr;
-  unsigned int *ticket = nullptr;
 };
 
 mrw_status chain_workspace(int dev, cudaStream_t stream, ChainWs *out) {
@@ -177,7 +176,6 @@ mrw_status chain_workspace(int dev, cudaStream_t stream, ChainWs *out) {
     return cuda_fail(e, "cudaMemset(workspace)");
   }
   w.partials = (unsigned long long *)p;
-  w.ticket = (unsigned int *)((uint8_t *)p + sizeof(unsigned long long) * 3 * kChainSlots);
   cache[key] = w;
   *out = w;
   return MRW_OK;
@@ -675,6 +673,7 @@ struct ChainReplay {
   mrw_config cfg{};
   ChainArgs a{};
   int n_noise = 0, unroll = 1, grid = 0, block = 0;
+  int finish_nout = 0;  // > 0: the MapReduce finish kernel follows the chain launch
 };
 
 struct Launch {  // everything one execute call enqueues
@@ -877,10 +876,10 @@ struct ChainShape {
 // thread's per-column hash halves serve many rows. Chains without them are pure streaming: every
 // thread takes `unroll` consecutive rows at a time in short CTAs that the hardware schedules as SMs
 // free up (measured on GB300: a 128 MiB copy in this order runs about 5 % faster than the one-wave
-// order). There the grid is capped at `waves` x sms x ctas_per_sm CTAs: 8 waves for a map, 2 for a
-// MapReduce group, whose CTAs each pay a finish (block reduction, adds, ticket).
+// order). There the grid is capped at 8 x sms x ctas_per_sm CTAs; in a MapReduce group each CTA
+// ends with a block reduction and three adds whose results it does not wait for.
 ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, int wg, int n_noise,
-                       bool mirror = false, bool query_occupancy = false, bool reduce = false) {
+                       bool mirror = false, bool query_occupancy = false) {
   ChainShape s;
   const int64_t col_vecs = (W + 15) / 16;
   if (n_noise == 0) {
@@ -894,7 +893,7 @@ ChainShape chain_shape(const mrw_config &cfg, int sms, int64_t W, int64_t rows, 
     s.unroll = cfg.unroll ? cfg.unroll : 4;
     s.blocked = true;
     const int64_t groups = (rows + s.unroll - 1) / s.unroll;
-    const int64_t max_ctas = std::min<int64_t>((int64_t)(reduce ? 2 : 8) * sms * cps, kMaxChainGrid);
+    const int64_t max_ctas = std::min<int64_t>((int64_t)8 * sms * cps, kMaxChainGrid);
     s.rows_parallel = std::max<int64_t>(1, std::min<int64_t>(groups, max_ctas * s.block / col_vecs));
     s.grid = (int)((s.rows_parallel * col_vecs + s.block - 1) / s.block);
     return s;
@@ -941,13 +940,13 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
     ChainWs ws;
     TRY(chain_workspace(L.device, L.stream, &ws));
     a.partials = ws.partials;
-    a.ticket = ws.ticket;
   }
-  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true,
-                                   a.reduce != RED_NONE);
+  const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true);
   if (s.grid > kMaxChainGrid) return fail(MRW_ERR_UNSUPPORTED, "chain grid above %d CTAs", kMaxChainGrid);
   s.apply(a);
   CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+  const int nout = a.reduce == RED_COUNT3 ? 3 : 1;
+  if (a.partials) CU(launch_chain_finish(a.partials, a.red, nout, L.stream));
   if (L.record) {
     ChainReplay &r = *L.record;
     r.a = a;
@@ -955,6 +954,7 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
     r.unroll = s.unroll;
     r.grid = s.grid;
     r.block = s.block;
+    r.finish_nout = a.partials ? nout : 0;
     L.recorded = true;
   }
   return MRW_OK;
@@ -1393,8 +1393,7 @@ mrw_status enqueue_image_overlapped(Launch &L, const Group &g, const View &vin, 
     a.out = (uint8_t *)dout + r0 * pitch;
     a.rows = nr;
     a.row0 = r0;
-    const ChainShape s = chain_shape(cfg, L.sms, geo.W, nr, wg, count_noise(g.pre), a.mirror != 0, true,
-                                     a.reduce != RED_NONE);
+    const ChainShape s = chain_shape(cfg, L.sms, geo.W, nr, wg, count_noise(g.pre), a.mirror != 0, true);
     s.apply(a);
     CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
     CU(cudaEventRecord(ev_k, L.stream));
@@ -1514,7 +1513,7 @@ void prepare_chain(const Group &g, const uint8_t *in, int64_t ip, uint8_t *out, 
   a.mirror = mirror_parity(g.pre);
   fill_ops(g.pre, a.mirror, a.ops);
   pr->n_noise = count_noise(g.pre);
-  pr->cs = chain_shape(cfg, sms, geo.W, geo.rows, wg, pr->n_noise, a.mirror != 0, true, g.reduce != RED_NONE);
+  pr->cs = chain_shape(cfg, sms, geo.W, geo.rows, wg, pr->n_noise, a.mirror != 0, true);
   pr->cs.apply(a);
 }
 
@@ -2236,7 +2235,8 @@ mrw_status replay_chain(const ChainReplay &r, bool timed, mrw_future_t *out) {
     return s;
   }
   if (timed) cudaEventRecord(f->start, r.stream);
-  const cudaError_t e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
+  cudaError_t e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
+  if (e == cudaSuccess && r.finish_nout > 0) e = launch_chain_finish(r.a.partials, r.a.red, r.finish_nout, r.stream);
   cudaEventRecord(f->done, r.stream);
   if (e != cudaSuccess) {
     const mrw_status st = cuda_fail(e, "chain kernel launch");
@@ -2663,8 +2663,7 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
           << ",\"grid\":" << stencil_grid(s, sa, tx * ty * geo.D, sms) << ",\"block\":" << s.block
           << ",\"smem\":" << s.smem;
       } else {
-        const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg, count_noise(g.pre), false, false,
-                                         g.reduce != RED_NONE);
+        const ChainShape s = chain_shape(c, sms, geo.W, geo.rows, p.wg, count_noise(g.pre), false, false);
         o << "\"kernel\":\"chain\",\"ops\":";
         ops_json(o, g.pre);
         ChainOp ops[kMaxChainOps];
@@ -2674,7 +2673,8 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
         o << ",\"reduce_only\":" << (g.reduce_only ? "true" : "false") << ",\"reduce\":" << g.reduce
           << ",\"nu\":16,\"col_vecs\":" << (geo.W + 15) / 16 << ",\"rows_parallel\":" << s.rows_parallel
           << ",\"grid\":" << s.grid << ",\"block\":" << s.block << ",\"unroll\":" << s.unroll
-          << ",\"order\":\"" << (s.blocked ? "blocked" : "persistent") << "\"";
+          << ",\"order\":\"" << (s.blocked ? "blocked" : "persistent") << "\""
+          << ",\"finish_kernel\":" << (g.reduce != RED_NONE ? "true" : "false");
       }
       o << "}";
     }

@@ -84,12 +84,12 @@ struct ChainArgs {
   int32_t blocked;
   unsigned long long *red; // RED_COUNT3: [3] counts; RED_SUM: [1]
   // MapReduce finish: with `partials` set (a per-stream workspace of kChainSlots sets of 3
-  // accumulators and a ticket, all zero between launches), CTA b adds into set b % kChainSlots and
-  // the last CTA to arrive (ticket) sums the sets into `red` and zeroes them again; spreading the
-  // adds over the sets keeps thousands of CTAs from queueing on one address. With `partials` null,
-  // CTAs add into a zeroed `red` (used when several launches accumulate into one result).
+  // accumulators, all zero between launches), CTA b adds into set b % kChainSlots and the finish
+  // kernel launched next on the stream (launch_chain_finish) sums the sets into `red` and zeroes
+  // them again; spreading the adds over the sets keeps thousands of CTAs from queueing on one
+  // address. With `partials` null, CTAs add into a zeroed `red` (used when several launches
+  // accumulate into one result).
   unsigned long long *partials;
-  unsigned int *ticket;
   int64_t row0;            // global row of the first row (the Offset trait, for the noise hash)
   int32_t pattern;         // OpPattern of ops[0, nops) (set by launch_chain)
   uint32_t pattern_t;      // PAT_THRESH thresholds
@@ -104,6 +104,9 @@ constexpr int kMaxChainGrid = 1 << 22;
 int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block);
 // n_noise: number of OP_NOISE entries (<= kMaxNoisePerGroup); unroll in {1, 2, 4, 8}.
 cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s);
+// The MapReduce finish of a chain launch with a workspace: one CTA that sums the kChainSlots sets of
+// `partials` into red[0, nout) and zeroes them; enqueue it right after that launch on the same stream.
+cudaError_t launch_chain_finish(unsigned long long *partials, unsigned long long *red, int nout, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Stencil (5x5 box blur) groups and batched instances, TMA-staged tiles
