@@ -92,7 +92,7 @@ def test_alternating_trees_and_a_mapreduce():
         assert np.array_equal(y.cpu().numpy(), want_lab) and np.array_equal(red.cpu().numpy(), want_counts)
         _run(filt, [x, y])
         assert np.array_equal(y.cpu().numpy(), want_filt)
-    for _ in range(3):  # the same MapReduce call back to back: replayed, counts reset by the kernel
+    for _ in range(3):  # the same MapReduce call back to back: replayed (chain and finish kernel), counts overwritten
         red.fill_(-1)
         _run(seg, [x, y, red])
         assert np.array_equal(red.cpu().numpy(), want_counts)
