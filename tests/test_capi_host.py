@@ -137,8 +137,10 @@ def test_mapreduce_fuses_into_the_last_chain_group(lib):
     args = _image_args(64, 512, d=8, reduce=True)
     d = mrw.plan_describe(mr, args, mrw.config())
     assert len(d["groups"]) == 1 and d["groups"][0]["reduce"] == 1
+    assert d["groups"][0]["finish_kernel"]  # the one-CTA finish runs behind the reducing launch
     u = mrw.plan_describe(mr, args, mrw.config(fusion=mrw.MRW_FUSE_NONE))
     assert len(u["groups"]) == 2 and u["groups"][1]["reduce_only"]
+    assert [g["finish_kernel"] for g in u["groups"]] == [False, True]
 
 
 def test_loops_of_image_stages_unroll_into_the_chain(lib):
