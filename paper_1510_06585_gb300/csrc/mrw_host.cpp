@@ -152,6 +152,9 @@ StatusPool &status_pool() {
 
 // Accumulators of the chain kernel's MapReduce finish: one set per (device, stream), so launches
 // that may overlap never share accumulators. The finish kernel leaves them at zero.
+// A reducing chain launch and its finish kernel must be adjacent on their stream (the finish sums
+// whatever the sets hold), so threads that share a stream enqueue the pair under this lock.
+std::mutex g_reduce_mu;
 struct ChainWs {
   unsigned long long *partials = nullptr;
 };
@@ -944,9 +947,14 @@ mrw_status run_chain(Launch &L, const Group &g, const uint8_t *in, int64_t ip, u
   const ChainShape s = chain_shape(cfg, L.sms, geo.W, geo.rows, wg, count_noise(g.pre), a.mirror != 0, true);
   if (s.grid > kMaxChainGrid) return fail(MRW_ERR_UNSUPPORTED, "chain grid above %d CTAs", kMaxChainGrid);
   s.apply(a);
-  CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
   const int nout = a.reduce == RED_COUNT3 ? 3 : 1;
-  if (a.partials) CU(launch_chain_finish(a.partials, a.red, nout, L.stream));
+  if (a.partials) {
+    std::lock_guard<std::mutex> lk(g_reduce_mu);
+    CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+    CU(launch_chain_finish(a.partials, a.red, nout, L.stream));
+  } else {
+    CU(launch_chain(a, count_noise(g.pre), s.unroll, s.grid, s.block, L.stream));
+  }
   if (L.record) {
     ChainReplay &r = *L.record;
     r.a = a;
@@ -2235,8 +2243,14 @@ mrw_status replay_chain(const ChainReplay &r, bool timed, mrw_future_t *out) {
     return s;
   }
   if (timed) cudaEventRecord(f->start, r.stream);
-  cudaError_t e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
-  if (e == cudaSuccess && r.finish_nout > 0) e = launch_chain_finish(r.a.partials, r.a.red, r.finish_nout, r.stream);
+  cudaError_t e;
+  if (r.finish_nout > 0) {
+    std::lock_guard<std::mutex> lk(g_reduce_mu);
+    e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
+    if (e == cudaSuccess) e = launch_chain_finish(r.a.partials, r.a.red, r.finish_nout, r.stream);
+  } else {
+    e = launch_chain(r.a, r.n_noise, r.unroll, r.grid, r.block, r.stream);
+  }
   cudaEventRecord(f->done, r.stream);
   if (e != cudaSuccess) {
     const mrw_status st = cuda_fail(e, "chain kernel launch");
