@@ -141,6 +141,14 @@ def test_mapreduce_fuses_into_the_last_chain_group(lib):
     u = mrw.plan_describe(mr, args, mrw.config(fusion=mrw.MRW_FUSE_NONE))
     assert len(u["groups"]) == 2 and u["groups"][1]["reduce_only"]
     assert [g["finish_kernel"] for g in u["groups"]] == [False, True]
+    # a reducing group's CTAs do not wait at their end, so it takes the map's launch shape
+    cfg = mrw.config(block=128, ctas_per_sm=8, unroll=8)
+    big = _image_args(512, 512, d=512, reduce=True)
+    g_red = mrw.plan_describe(mr, big, cfg)["groups"][0]
+    g_map = mrw.plan_describe(mrw.map_(mrw.stage("threshold3")), big[:2], cfg)["groups"][0]
+    assert (g_red["grid"], g_red["block"], g_red["rows_parallel"]) == (g_map["grid"], g_map["block"],
+                                                                       g_map["rows_parallel"])
+    assert g_red["grid"] * g_red["block"] == g_red["rows_parallel"] * g_red["col_vecs"] and g_red["order"] == "blocked"
 
 
 def test_loops_of_image_stages_unroll_into_the_chain(lib):
