@@ -5,6 +5,7 @@ import os
 import numpy as np
 import pytest
 import torch
+from scipy.spatial import cKDTree
 
 from oracle import nbody as O
 from paper_1510_06585_gb300 import inputs
@@ -13,7 +14,7 @@ from paper_1510_06585_gb300 import mrw as M
 pytestmark = pytest.mark.gpu
 
 EPS, DT = 1e-3, 1e-3
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "nbody_65536_100steps.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "nbody_65536_100steps.npz")
 
 
 def _state(n, seed=inputs.SEED_NBODY):
@@ -57,15 +58,46 @@ def test_two_body_closed_form_on_gpu():
     assert np.allclose(a[1, :3], [-mag, 0, 0], rtol=2e-6, atol=0)
 
 
+def _nearest(x4):
+    p = np.asarray(x4, np.float64)[:, :3]
+    return cKDTree(p).query(p, k=2)[0][:, 1]
+
+
+def _velocity_errors(vg, vr):
+    """Per-body |v - v^| / max_j |v^_j| (velocities start at 0, so they take a global scale)."""
+    vr = np.asarray(vr, np.float64)[:, :3]
+    return np.linalg.norm(np.asarray(vg, np.float64)[:, :3] - vr, axis=1) / np.linalg.norm(vr, axis=1).max()
+
+
+def _report(tag, dv, min_sep):
+    close = min_sep < 10 * EPS
+    print(f"{tag}: velocity error max {dv.max():.3e}; bodies that came within 10 eps of another "
+          f"({close.sum()}): max {dv[close].max() if close.any() else 0:.3e}; the others "
+          f"({(~close).sum()}): max {dv[~close].max():.3e}; of the bodies above 1e-4, "
+          f"{(close & (dv > 1e-4)).sum()} of {(dv > 1e-4).sum()} came within 10 eps")
+
+
 def test_100_steps_n4096_within_1e_4_of_fp64():
     n = 4096
     st, x = _state(n)
     _run(_tree(100), st)
-    xs, vs, _ = O.simulate(x, 100)
-    # the gate is the position error (1e-4); velocities start at 0 and are dominated by the few
-    # close pairs inside the softening length, so they get a looser sanity bound
+    # the oracle stepped one kick-drift-kick step at a time (bit-identical to one 100-step run),
+    # recording each body's closest approach to any other body
+    g = O.gravity(n)
+    xs, vs, acc = np.asarray(x, np.float64), np.zeros((n, 3)), O.accel(x, g)
+    min_sep = _nearest(xs)
+    for _ in range(100):
+        xs, vs, acc = O.kdk(xs, vs, acc, 1, g)
+        min_sep = np.minimum(min_sep, _nearest(xs))
     assert O.pos_rel_error(st[0].cpu().numpy(), xs) <= 1e-4
-    assert O.vel_rel_error(st[1].cpu().numpy(), vs) <= 1e-2
+    # Velocities: the FP32 rounding of d = x_j - x_i is amplified for a pair closer than the
+    # softening length (a GB300 run: 1.3e-3 for the two bodies of a pair at 0.1 eps, 1.2e-4 for every
+    # body that never came within eps, 1.1e-5 for those that never came within 10 eps).
+    dv = _velocity_errors(st[1].cpu().numpy(), vs)
+    _report("N=4096", dv, min_sep)
+    assert dv[min_sep >= 10 * EPS].max() <= 1e-4
+    assert dv[min_sep >= EPS].max() <= 1e-3
+    assert dv.max() <= 1e-2
     xg = st[0].cpu().numpy().astype(np.float64)
     p = O.momentum(xg, st[1].cpu().numpy())
     assert np.linalg.norm(p) <= 1e-4 * (xg[:, 3:4] * np.abs(st[1].cpu().numpy()[:, :3])).sum()
@@ -109,15 +141,22 @@ def test_full_size_65536_bodies_100_steps_against_fp64_trajectory():
     n = 65536
     st, x = _state(n)
     _run(_tree(100), st)
-    rows = np.loadtxt(GOLDEN)
-    idx = rows[:, 0].astype(np.int64)
+    gold = np.load(GOLDEN)
     xg = st[0].cpu().numpy()
     vg = st[1].cpu().numpy()
-    assert O.pos_rel_error(xg[idx], rows[:, 1:4]) <= 1e-4
-    vr = rows[:, 4:7]
-    assert np.abs(vg[idx, :3] - vr).max() <= 1e-2 * np.linalg.norm(vr, axis=1).max()
+    # every body's position within the workload's 1e-4 bound of the FP64 trajectory
+    assert O.pos_rel_error(xg, gold["x"]) <= 1e-4
+    # every body's velocity within 1e-3 of max |v^| (a GB300 run: 4.1e-4, all of the 129 bodies above
+    # 1e-4 having come within 10 eps of another body), and within 1e-4 for the 45626 bodies that
+    # never came within 10 eps (that run: 7.4e-6)
+    dv = _velocity_errors(vg, gold["v"])
+    _report("N=65536", dv, gold["min_sep"])
+    assert dv.max() <= 1e-3
+    assert dv[gold["min_sep"] >= 10 * EPS].max() <= 1e-4
+    p = O.momentum(xg, vg)
+    assert np.linalg.norm(p) <= 1e-4 * (xg[:, 3:4].astype(np.float64) * np.abs(vg[:, :3])).sum()
     # sampled single-step accelerations of the final state
-    samp = idx[:64]
+    samp = np.arange(0, n, 1024)
     a_ref = O.accel_of(xg, samp, 1.0 / n)
     st2 = [st[0].clone(), st[1].clone(), torch.zeros_like(st[2])]
     _run(_tree(0), st2)
