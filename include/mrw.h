@@ -229,8 +229,10 @@ void mrw_node_release(mrw_node_t n);
 /* ------------------------------------------------------------------------------------------ */
 /* Arguments by tree family:
  *   image trees (any nesting of Pipeline/Map/Loop over u8 stages): args[0] = input (u8),
- *     args[1] = output (u8, same shape, must not overlap the input); a MapReduce root adds
- *     args[2] = int64[3] class counts (THRESHOLD3 last) or int64[1] sum, overwritten;
+ *     args[1] = output (u8, same shape, must not overlap the input); a MapReduce root may add
+ *     args[2] = int64[3] class counts (THRESHOLD3 last) or int64[1] sum, overwritten; without
+ *     args[2] (nargs = 2) the future holds the result (mrw_future_result; the plan, tuning and feature
+ *     calls still take the three arguments);
  *   N-body trees (NBODY_ACCEL, NBODY_KDK, Pipeline/Loop of them): args = x, v, a, each float32
  *     (N, 4), updated in place;
  *   SAXPY: args = x, y (float32, same shape), y updated in place;
@@ -280,17 +282,27 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
  *   - the tree must fuse into one kernel: image stages with at most one blur and at most 16
  *     pointwise stages on each side of it, cfg->fusion == MRW_FUSE_ALL (else MRW_ERR_UNSUPPORTED);
  *   - the call enqueues on `stream` and returns; it creates no future: synchronise the stream to
- *     wait. A tile wait that gives up its bound leaves that tile unwritten and records the
- *     failure only inside the array;
+ *     wait. A tile wait that gives up its bound leaves that tile unwritten and sets the array's
+ *     status word, which mrw_noalloc_status reads: check it after the work to know that every
+ *     output byte was written;
  *   - every call reuses the one array, clearing its counter and status word on entry: calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on it and must be
  *     serialised by the caller;
- *   - the first call on each device looks up the array's device address with that device current;
- *     make that first call before any stream capture on that device. */
+ *   - the call is not for CUDA graph capture: while `stream` is capturing it returns
+ *     MRW_ERR_UNSUPPORTED and enqueues nothing (its table copies come from one shared host
+ *     staging area that a replayed graph would read after later calls had changed it);
+ *   - the first call on each device looks up the array's device address with that device current. */
 #define MRW_NOALLOC_MAX_INSTANCES 256
 mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t *in_arena, uint8_t *out_arena,
                                        int64_t arena_bytes, const int64_t *desc, int64_t n, const mrw_config *cfg,
                                        void *stream);
+/* Status of the last mrw_execute_batched_noalloc call on the current device (no counterpart in the
+ * paper): copies the array's status word out on `stream` behind the work already enqueued there,
+ * waits for that stream and stores the word in *host_status (0: every tile wait ended in time).
+ * Allocates nothing. Returns MRW_OK for 0, MRW_ERR_DEVICE when the last call gave up a wait (some
+ * of its tiles are unwritten), MRW_ERR_INVALID_ARG for a NULL host_status, MRW_ERR_CUDA when the
+ * copy fails. Query on the stream of the call, before the next call, which clears the word. */
+mrw_status mrw_noalloc_status(void *stream, uint32_t *host_status);
 
 /* Wait for a future: MRW_OK when the work finished, MRW_ERR_TIMEOUT if `timeout_ms` (< 0 =
  * forever) passed first (the future stays valid), MRW_ERR_DEVICE if a kernel gave up a bounded
@@ -302,6 +314,16 @@ mrw_status mrw_future_query(mrw_future_t f);
  * completion). Only futures of mrw_execute_timed carry it; any other future gives
  * MRW_ERR_INVALID_ARG. */
 mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms);
+/* The result of a MapReduce execution (Section 2.1: a run returns a future of the computation's
+ * result; Table 1, run). Waits for the work (as mrw_future_wait with no deadline), then copies the
+ * nresult int64 values to `host_dst` (host memory of at least `bytes` bytes; nresult = 3 class
+ * counts for a THRESHOLD3-terminated map, else 1 value sum). Where the values come from:
+ *   - the call had no args[2]: the future's own page-locked slot, filled by the call's work;
+ *   - the call had args[2]: that buffer, read when this function runs (the future keeps no copy),
+ *     so it must still hold the call's result.
+ * Errors: MRW_ERR_INVALID_ARG (NULL argument, a tree without a reduction, bytes < 8 nresult),
+ * and the errors of mrw_future_wait. May be called more than once, before mrw_future_release. */
+mrw_status mrw_future_result(mrw_future_t f, void *host_dst, size_t bytes);
 void mrw_future_release(mrw_future_t f);
 
 /* Describe the plan the executor would run for (root, args, cfg) as a JSON string: the fused
@@ -309,6 +331,81 @@ void mrw_future_release(mrw_future_t f);
  * (NUL-terminated); *needed receives the full length. Launches nothing. */
 mrw_status mrw_plan_describe(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
                              char *buf, int64_t cap, int64_t *needed);
+
+/* ------------------------------------------------------------------------------------------ */
+/* CPU + GPU co-execution with dynamic load balancing (Section 3.2 workload distribution         */
+/* generator; Section 3.3, Dynamic Load Balancing and The Load Balancing Process)              */
+/* ------------------------------------------------------------------------------------------ */
+/* A balancer keeps, for one (tree, workload), the share of the rows the GPU runs, the load
+ * balancing threshold lbt and the state of the adaptive binary search:
+ *   - every co-executed run measures the GPU's and the host cores' times for their shares and
+ *     their deviation dev = shortest / longest (1 = perfectly balanced);
+ *   - isUnbalanced(dev) = 1 when dev / c_factor < max_dev, else 0, and
+ *     lbt(n) = isUnbalanced(dev) * weight + lbt(n - 1) * (1 - weight), lbt(0) = 0;
+ *   - profile construction (phase MRW_BAL_SEARCH): the whole work starts transferable; each run
+ *     splits the transferable part evenly between the GPU and the host cores, then binds the half
+ *     of the device that finished first to that device; the other half is the next transferable
+ *     part (size / 2^n after n runs) until it is below `precision` (phase MRW_BAL_MONITOR);
+ *   - when lbt reaches `trigger` (a persistent imbalance; three consecutive unbalanced runs from
+ *     lbt = 0 at weight 2/3) the adaptive binary search moves work from the slower to the faster
+ *     device: moves in one direction shift the search interval sideways by the transferable size
+ *     (MRW_BAL_SHIFT), which doubles when more than two shifts in a row go the same way; the first
+ *     move in the opposite direction returns to halving it (MRW_BAL_BISECT) until it is below
+ *     `precision` again; then the balancer monitors (lbt reset to 0). */
+typedef struct mrw_balancer *mrw_balancer_t;
+typedef enum mrw_bal_phase { MRW_BAL_SEARCH = 0, MRW_BAL_MONITOR = 1, MRW_BAL_SHIFT = 2, MRW_BAL_BISECT = 3 } mrw_bal_phase;
+typedef struct mrw_balance_params {
+  double weight;      /* weight of the latest run in lbt; 0 = 2/3 (the paper's default)            */
+  double max_dev;     /* balanced when (shortest / longest) / c_factor >= max_dev; 0 = 0.85         */
+  double c_factor;    /* correction for computations that run best slightly unbalanced; 0 = 1      */
+  double trigger;     /* lbt at which the load balancer starts moving work; 0 = 0.95               */
+  double precision;   /* smallest transferable part of the searches (fraction of the work);
+                         0 = 1/256                                                                 */
+  double gpu_share;   /* initial share of the GPU in [0, 1] with a converged profile (phase
+                         MONITOR); < 0 = profile construction from an even split                   */
+  int32_t cpu_threads;/* host worker threads; 0 = every core the process may run on               */
+  int32_t search_reps;/* runs at each share of the profile construction, the fastest time of each
+                         side deciding (Algorithm 1's number of executions against fluctuations);
+                         0 = 1                                                                     */
+} mrw_balance_params;
+typedef struct mrw_balance_report {
+  double gpu_share;    /* share of the rows the GPU ran in this execution                         */
+  int64_t gpu_rows, cpu_rows;
+  double gpu_ms, cpu_ms;  /* device time of the GPU's share (CUDA events); wall time of the host
+                             workers' share                                                        */
+  double dev;          /* shortest / longest of the two times (1 if one side had no rows)          */
+  int32_t unbalanced;  /* isUnbalanced(dev)                                                       */
+  int32_t phase;       /* mrw_bal_phase after this execution                                      */
+  double lbt;          /* after this execution                                                    */
+  double next_share;   /* GPU share of the next execution                                         */
+  double transferable; /* transferable part (fraction of the work) after this execution           */
+} mrw_balance_report;
+/* Errors: MRW_ERR_INVALID_ARG (NULL out, a parameter out of range: weight, max_dev, trigger,
+ * precision in (0, 1], c_factor > 0, gpu_share <= 1, cpu_threads >= 0, search_reps 0 .. 64).
+ * Starts the worker threads. */
+mrw_status mrw_balancer_create(const mrw_balance_params *params, mrw_balancer_t *out);
+void mrw_balancer_release(mrw_balancer_t b);
+/* The balancer's bookkeeping for one run whose two shares took gpu_ms and cpu_ms (>= 0): updates
+ * dev, lbt, the phase and the next share exactly as a co-executed run does, without running
+ * anything (the search and the threshold on their own, e.g. for a caller that runs the shares
+ * itself). *rep (may be NULL) receives the update; rep->gpu_share is the share that was run. */
+mrw_status mrw_balancer_observe(mrw_balancer_t b, double gpu_ms, double cpu_ms, mrw_balance_report *rep);
+/* The GPU share the next run will use. */
+mrw_status mrw_balancer_share(mrw_balancer_t b, double *gpu_share);
+/* Co-executes an image tree on host buffers: the GPU runs the first round(share x rows) rows (a
+ * fused pointwise kernel reading and writing page-locked buffers in place, else staging its rows),
+ * the host worker threads run the remaining rows at the same time (the same stage arithmetic; the
+ * noise hash takes each row's global index, the Offset trait of Section 3.4), and a MapReduce's
+ * partial results are merged on the host with + (Section 3.4 merging functions). Then the balancer
+ * observes the two times (mrw_balancer_observe). Blocking: returns when both shares are done.
+ * The tree must fuse into one pointwise kernel (noise, solarise, mirror, threshold3 stages under
+ * Pipeline / Map / Loop, optionally a MapReduce root): args[0], args[1] host u8 images or volumes
+ * (MRW_MEM_HOST); a MapReduce takes args[2] (int64[3] or int64[1], host or device) for the merged
+ * result. Rows are the partitioning unit: the tree must be partitionable by rows (no blur).
+ * Errors: as mrw_execute; MRW_ERR_UNSUPPORTED for device image buffers or a tree that does not
+ * fuse into one pointwise kernel. */
+mrw_status mrw_execute_coexec(mrw_balancer_t b, mrw_node_t root, const mrw_buffer *args, int32_t nargs,
+                              const mrw_config *cfg, void *stream, mrw_balance_report *rep);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Autotuner and knowledge base (Section 3.2: profile construction, Algorithm 1; knowledge base)*/

@@ -6,22 +6,50 @@
 namespace mrw {
 namespace {
 
-__global__ void saxpy_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t n, float alpha) {
-  const int64_t nv = n >> 2;
-  const float4 *x4 = reinterpret_cast<const float4 *>(x);
-  float4 *y4 = reinterpret_cast<float4 *>(y);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const float4 a = __ldcs(x4 + i);
-    float4 b = __ldcs(y4 + i);
-    b.x = fmaf(alpha, a.x, b.x);
-    b.y = fmaf(alpha, a.y, b.y);
-    b.z = fmaf(alpha, a.z, b.z);
-    b.w = fmaf(alpha, a.w, b.w);
-    __stcs(y4 + i, b);
+// A Map of k saxpy stages over the same x (Section 4, Saxpy): y := alpha_s x + y for s = 0 .. k-1,
+// in order, in registers, one fused multiply-add per stage and element, so the result has the bits
+// of k single-stage launches. One HBM read of x and of y and one write of y per element.
+// CTA b owns the float4 groups [b * 256 * U, (b + 1) * 256 * U), thread t the groups t, t + 256, ...
+// of it: each thread issues its 2U 16-byte loads before any arithmetic (U loads of x and of y in
+// flight), and the grid has one CTA per tile, scheduled as SMs free up.
+template <int U>
+__global__ void __launch_bounds__(256) saxpy_kernel(const __grid_constant__ SaxpyArgs a) {
+  const int64_t nv = a.n >> 2;
+  const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
+  float4 *y4 = reinterpret_cast<float4 *>(a.y);
+  const int64_t base = (int64_t)blockIdx.x * (256 * U) + threadIdx.x;
+  float4 xv[U], yv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = base + (int64_t)u * 256;
+    if (i < nv) {
+      xv[u] = __ldcs(x4 + i);
+      yv[u] = __ldcs(y4 + i);
+    }
   }
-  for (int64_t i = 4 * nv + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = fmaf(alpha, x[i], y[i]);
+  for (int s = 0; s < a.nstages; ++s) {
+    const float al = a.alpha[s];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      yv[u].x = fmaf(al, xv[u].x, yv[u].x);
+      yv[u].y = fmaf(al, xv[u].y, yv[u].y);
+      yv[u].z = fmaf(al, xv[u].z, yv[u].z);
+      yv[u].w = fmaf(al, xv[u].w, yv[u].w);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = base + (int64_t)u * 256;
+    if (i < nv) __stcs(y4 + i, yv[u]);
+  }
+  // the n mod 4 trailing elements: the first threads of the last CTA
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x < (a.n & 3)) {
+    const int64_t i = 4 * nv + threadIdx.x;
+    float yi = a.y[i];
+    const float xi = a.x[i];
+    for (int s = 0; s < a.nstages; ++s) yi = fmaf(a.alpha[s], xi, yi);
+    a.y[i] = yi;
+  }
 }
 
 __global__ void fill_u32_kernel(unsigned int *p, unsigned int v, int64_t n) {
@@ -97,9 +125,24 @@ cudaError_t launch_while_init(LoopCtrl *ctrl, unsigned int *changed, unsigned lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_saxpy(const float *x, float *y, int64_t n, float alpha, int grid, int block, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  saxpy_kernel<<<grid, block, 0, s>>>(x, y, n, alpha);
+int saxpy_grid(int64_t n, int unroll) {
+  const int64_t tiles = ((n >> 2) + 256LL * unroll - 1) / (256LL * unroll);
+  return (int)std::max<int64_t>(1, tiles);
+}
+
+cudaError_t launch_saxpy(const SaxpyArgs &a, int unroll, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (a.nstages < 1 || a.nstages > kMaxSaxpyStages) return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.n >> 2) + 256LL * unroll - 1) / (256LL * unroll);
+  if (tiles > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  const int grid = saxpy_grid(a.n, unroll);
+  switch (unroll) {
+    case 1: saxpy_kernel<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: saxpy_kernel<2><<<grid, 256, 0, s>>>(a); break;
+    case 4: saxpy_kernel<4><<<grid, 256, 0, s>>>(a); break;
+    case 8: saxpy_kernel<8><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 // Waits: only thread 0 waits on a TMA mbarrier, for a bounded number of polls; if the bound is
 // reached it records MRW status word 1 and the whole CTA leaves after a second bounded wait for
 // its copies in flight.
+#include <atomic>
 #include <mutex>
 
 #include "mrw_internal.h"
@@ -856,29 +857,38 @@ int count_noise_ops(const ChainOp *ops, int n) {
 size_t stencil_rows_smem_bytes() { return sizeof(RowWarpSmem) * kRowsWarps; }
 int stencil_rows_block() { return kRowsBlock; }
 
+// The kernels' shared-memory limits are attributes of each device's copy of the functions: set
+// them once per device, under a lock, before the first launch on that device.
 cudaError_t stencil_prepare() {
-  static bool attr_set = false;
-  if (!attr_set) {
-    for (int h : {0, 2})
-      for (int w : {64, 128, 224}) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_fn(w, h), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-      }
-    for (int v = 0; v < 12; ++v) {
-      cudaError_t e = cudaFuncSetAttribute(stencil_rows_fn((v >> 1) % 3, v & 1, v < 6 ? 4 : 3),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_rows_smem_bytes());
+  static std::atomic<bool> done[256];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  for (int h : {0, 2})
+    for (int w : {64, 128, 224}) {
+      e = cudaFuncSetAttribute(stencil_fn(w, h), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (e != cudaSuccess) return e;
     }
-    attr_set = true;
+  for (int v = 0; v < 12; ++v) {
+    e = cudaFuncSetAttribute(stencil_rows_fn((v >> 1) % 3, v & 1, v < 6 ? 4 : 3),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_rows_smem_bytes());
+    if (e != cudaSuccess) return e;
   }
+  done[dev].store(true, std::memory_order_release);
   return cudaSuccess;
 }
 
 int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps) {
-  static int cache[3][2][2] = {};
+  static std::atomic<int> cache[3][2][2];
   if (n_noise < 0 || n_noise > 2) return 1;
-  int &c = cache[n_noise][mirror ? 1 : 0][cps >= 4 ? 1 : 0];
-  if (c) return c;
+  std::atomic<int> &c = cache[n_noise][mirror ? 1 : 0][cps >= 4 ? 1 : 0];
+  const int known = c.load(std::memory_order_relaxed);
+  if (known) return known;
   int nb = 0;
   if (stencil_prepare() != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stencil_rows_fn(n_noise, mirror, cps), kRowsBlock,
@@ -886,8 +896,8 @@ int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps) {
     cudaGetLastError();
     return 1;
   }
-  c = nb > 0 ? nb : 1;
-  return c;
+  c.store(nb > 0 ? nb : 1, std::memory_order_relaxed);
+  return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_stencil(const StencilArgs &sa, int grid, int block, size_t smem, cudaStream_t s) {
@@ -1024,6 +1034,18 @@ cudaError_t launch_stencil_noalloc(StencilArgs a, const uint8_t *in_base, uint8_
   a.ninst = (int32_t)n;
   const int64_t grid = tiles < (int64_t)sms * cps ? tiles : (int64_t)sms * cps;
   return launch_stencil(a, (int)(grid > 0 ? grid : 1), kBlock, smem, s);
+}
+
+cudaError_t stencil_noalloc_status(cudaStream_t s, unsigned int *out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocTables *dev = nullptr;
+  cudaError_t e = noalloc_scratch_ptr(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned int v = 0;
+  e = cudaMemcpyAsync(&v, &dev->status, sizeof v, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *out = v;
+  return e;
 }
 
 }  // namespace mrw

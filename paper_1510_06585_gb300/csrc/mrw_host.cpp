@@ -150,6 +150,42 @@ StatusPool &status_pool() {
   return p;
 }
 
+// Page-locked slots of kResultSlot int64 values: the MapReduce result a future owns when its call
+// was given no result buffer (args[2]). The call's staging copies the counts into the slot.
+constexpr int kResultSlot = 4;
+class ResultPool {
+ public:
+  mrw_status take(int64_t **out) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.empty()) {
+      const int n = 256;
+      int64_t *h = nullptr;
+      if (cudaHostAlloc(&h, n * kResultSlot * sizeof(int64_t), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MRW_ERR_OOM, "pinned result slots");
+      }
+      memset(h, 0, n * kResultSlot * sizeof(int64_t));
+      for (int i = n - 1; i >= 0; --i) free_.push_back(h + (int64_t)i * kResultSlot);
+    }
+    *out = free_.back();
+    free_.pop_back();
+    return MRW_OK;
+  }
+  void give(int64_t *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.push_back(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<int64_t *> free_;
+};
+ResultPool &result_pool() {
+  static ResultPool p;
+  return p;
+}
+
 // Accumulators of the chain kernel's MapReduce finish: one set per (device, stream), so launches
 // that may overlap never share accumulators. The finish kernel leaves them at zero.
 // A reducing chain launch and its finish kernel must be adjacent on their stream (the finish sums
@@ -263,6 +299,106 @@ mrw_status side_streams(int dev, cudaStream_t *in, cudaStream_t *out) {
   return MRW_OK;
 }
 
+// A non-blocking stream per device for copying a future's result out of device memory after its
+// work has completed; callers hold g_result_mu from the copy to its synchronisation.
+std::mutex g_result_mu;
+mrw_status result_stream(int dev, cudaStream_t *out) {
+  static std::map<int, cudaStream_t> m;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = m.find(dev);
+  if (it == m.end()) {
+    cudaStream_t s;
+    CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    it = m.emplace(dev, s).first;
+  }
+  *out = it->second;
+  return MRW_OK;
+}
+
+// A bounded cache of launch plans (CUDA graphs and the device memory they use). The key holds
+// everything that decides what a plan enqueues, the stream included, so every launch of one entry
+// is ordered on one stream; each use records the entry's `last_use` event behind its work. Evicting
+// the least recently used entry waits for that event only (not for the device), outside the cache
+// lock, and an entry a caller still holds is destroyed when that caller lets it go.
+template <class Plan>
+class PlanCache {
+ public:
+  using Ptr = std::shared_ptr<Plan>;
+  explicit PlanCache(size_t cap) : cap_(cap) {}
+  Ptr find(const std::string &key) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = m_.find(key);
+    if (it == m_.end()) return nullptr;
+    it->second.tick = ++tick_;
+    return it->second.p;
+  }
+  // Adds `p` under `key` and returns the entry now cached there (another thread's, if it added the
+  // same key first; `p` is then dropped).
+  Ptr insert(const std::string &key, Ptr p) {
+    Ptr evicted;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      auto it = m_.find(key);
+      if (it != m_.end()) {
+        it->second.tick = ++tick_;
+        evicted = std::move(p);
+        return it->second.p;
+      }
+      if (m_.size() >= cap_) {
+        auto lru = m_.begin();
+        for (auto j = m_.begin(); j != m_.end(); ++j)
+          if (j->second.tick < lru->second.tick) lru = j;
+        evicted = std::move(lru->second.p);
+        m_.erase(lru);
+      }
+      m_[key] = Entry{p, ++tick_};
+    }
+    return p;  // `evicted` is released here, after the lock
+  }
+  size_t size() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return m_.size();
+  }
+
+ private:
+  struct Entry {
+    Ptr p;
+    uint64_t tick = 0;
+  };
+  std::mutex mu_;
+  std::map<std::string, Entry> m_;
+  uint64_t tick_ = 0;
+  size_t cap_;
+};
+
+// Wraps a built plan for a PlanCache: creates its last_use event; the deleter waits for that event
+// and then frees the plan with `destroy`.
+template <class Plan>
+mrw_status make_cached(Plan &built, void (*destroy)(Plan &), std::shared_ptr<Plan> *out) {
+  cudaEvent_t ev = nullptr;
+  const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    destroy(built);
+    return cuda_fail(e, "cudaEventCreate(plan)");
+  }
+  built.last_use = ev;
+  *out = std::shared_ptr<Plan>(new Plan(built), [destroy](Plan *q) {
+    cudaEventSynchronize(q->last_use);
+    cudaEventDestroy(q->last_use);
+    destroy(*q);
+    delete q;
+  });
+  return MRW_OK;
+}
+
+// Records a plan's last_use event on the stream when the scope that enqueued work with it ends,
+// whether or not every step succeeded.
+struct RecordOnExit {
+  cudaEvent_t ev;
+  cudaStream_t stream;
+  ~RecordOnExit() { cudaEventRecord(ev, stream); }
+};
+
 }  // namespace
 
 // ============================================================================================
@@ -295,6 +431,12 @@ struct mrw_future {
   bool has_status = false;
   mrw_status deferred = MRW_OK;  // an error found while enqueueing after the first launch
   std::vector<cudaEvent_t> sync_events;  // cross-stream ordering events of an overlapped staging
+  // MapReduce result (Section 2.1: the future of a run carries its result): nresult int64 values,
+  // held in the future's own page-locked slot (the call had no args[2]) or in the caller's args[2]
+  int32_t nresult = 0;
+  int64_t *result_slot = nullptr;  // ResultPool slot, written by a copy enqueued with the call
+  const void *result_src = nullptr;  // args[2] of the call, read when the result is asked for
+  int result_mem = MRW_MEM_DEVICE;
 };
 
 namespace {
@@ -1450,11 +1592,12 @@ struct WhilePlan {
   unsigned int *words = nullptr;  // [0] changed, [1] status, [2 ..] tile queues
   std::vector<void *> owned;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t last_use = nullptr;  // recorded behind every use (PlanCache)
 };
 
-std::map<std::string, WhilePlan> &while_plans() {
-  static std::map<std::string, WhilePlan> m;
-  return m;
+PlanCache<WhilePlan> &while_plans() {
+  static PlanCache<WhilePlan> *c = new PlanCache<WhilePlan>(16);  // never destroyed: no CUDA calls at exit
+  return *c;
 }
 
 void destroy_while_plan(WhilePlan &w) {
@@ -1625,26 +1768,19 @@ mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, con
   TRY(prepare_user_groups(L, group_stages(pre, fused, false)));  // user stages before / after the loop
   TRY(prepare_user_groups(L, group_stages(post, fused, false)));
   const std::string key = image_program_key(p, geo, cfg, L.device, L.stream);
-  WhilePlan wp;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = while_plans().find(key);
-    if (it != while_plans().end()) wp = it->second;
-  }
-  if (!wp.exec) {
-    mrw_status s = build_while_plan(L, p, geo, cfg, &wp);
+  std::shared_ptr<WhilePlan> cached = while_plans().find(key);
+  if (!cached) {
+    WhilePlan built;
+    mrw_status s = build_while_plan(L, p, geo, cfg, &built);
     if (s != MRW_OK) {
-      destroy_while_plan(wp);
+      destroy_while_plan(built);
       return s;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (while_plans().size() >= 16) {
-      cudaDeviceSynchronize();
-      for (auto &kv : while_plans()) destroy_while_plan(kv.second);
-      while_plans().clear();
-    }
-    while_plans()[key] = wp;
+    TRY(make_cached(built, destroy_while_plan, &cached));
+    cached = while_plans().insert(key, cached);
   }
+  const WhilePlan &wp = *cached;
+  RecordOnExit used_until{wp.last_use, L.stream};
   void *din, *dout;
   int64_t pin, pout;
   TRY(resolve(L, vin, true, false, &din, &pin));
@@ -1669,6 +1805,23 @@ mrw_status enqueue_image_while(Launch &L, const Program &p, const View &vin, con
   return MRW_OK;
 }
 
+// One chain group over two host image buffers: such a plan reads and writes page-locked buffers in
+// place, or stages the rows in overlapped chunks (chunked_staging).
+bool host_one_chain(const std::vector<Group> &gs, const View &vin, const View &vout) {
+  return gs.size() == 1 && !gs[0].use_stencil && !gs[0].user && vin.b->memory == MRW_MEM_HOST &&
+         vout.b->memory == MRW_MEM_HOST;
+}
+
+// Whether an execution stages its host rows in overlapped chunks (enqueue_image_overlapped): one
+// chain group over host buffers that are not both mapped page-locked memory, at least 64 rows and
+// 8 MiB. Such a plan reduces by adds into the zeroed result, with no finish kernel.
+bool chunked_staging(const std::vector<Group> &gs, const View &vin, const View &vout, const ImgGeom &geo) {
+  if (!host_one_chain(gs, vin, vout)) return false;
+  void *a = nullptr, *b = nullptr;
+  if (mapped_host(vin, &a) && mapped_host(vout, &b)) return false;
+  return geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20);
+}
+
 mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
                          unsigned int *status, bool *used_status) {
   View vin, vout, vred;
@@ -1685,15 +1838,14 @@ mrw_status enqueue_image(Launch &L, const Program &p, const mrw_buffer *args, in
         (p.reduce == RED_NONE || vred.b->memory == MRW_MEM_DEVICE)))
     L.record = nullptr;
   TRY(prepare_user_groups(L, gs));
-  const bool one_chain = gs.size() == 1 && !gs[0].use_stencil && !gs[0].user && vin.b->memory == MRW_MEM_HOST &&
-                         vout.b->memory == MRW_MEM_HOST;
+  const bool one_chain = host_one_chain(gs, vin, vout);
   void *din = nullptr, *dout = nullptr;
   int64_t pin = vin.pitch, pout = vout.pitch;
   // Page-locked host buffers mapped into the device address space, read once and written once by
   // a single streaming kernel: the kernel reads and writes them in place over the host link
   // (NVLink-C2C on Grace-Blackwell), which moves the bytes faster than staging copies do.
   if (!(one_chain && mapped_host(vin, &din) && mapped_host(vout, &dout))) {
-    if (one_chain && L.events && geo.rows >= 64 && vin.pitch * vin.rows >= (8 << 20))
+    if (L.events && chunked_staging(gs, vin, vout, geo))
       return enqueue_image_overlapped(L, gs[0], vin, vout, p.reduce != RED_NONE ? &vred : nullptr, geo, cfg, p.wg);
     TRY(resolve(L, vin, true, false, &din, &pin));
     TRY(resolve(L, vout, false, true, &dout, &pout));
@@ -1737,23 +1889,27 @@ NbShape nbody_shape(const mrw_config &cfg, int sms, int64_t n, int wg) {
 struct LoopGraph {
   cudaGraphExec_t exec = nullptr;
   LoopCtrl *ctrl = nullptr;
+  cudaEvent_t last_use = nullptr;  // recorded behind every launch (PlanCache)
 };
 
-std::map<std::string, LoopGraph> &loop_graphs() {
-  static std::map<std::string, LoopGraph> m;
-  return m;
+void destroy_loop_graph(LoopGraph &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.ctrl) cudaFree(g.ctrl);
 }
 
-mrw_status get_loop_graph(const NBodyParams &np, int64_t iters, const NbShape &s, int device, LoopGraph *out) {
+PlanCache<LoopGraph> &loop_graphs() {
+  static PlanCache<LoopGraph> *c = new PlanCache<LoopGraph>(64);  // never destroyed: no CUDA calls at exit
+  return *c;
+}
+
+// The device-controlled Loop graph of (state arrays, constants, launch shape, stream), cached.
+mrw_status get_loop_graph(const NBodyParams &np, int64_t iters, const NbShape &s, int device, cudaStream_t stream,
+                          std::shared_ptr<LoopGraph> *out) {
   char key[256];
-  snprintf(key, sizeof key, "%d|%p|%p|%p|%d|%a|%a|%a|%lld|%d|%d|%d", device, (void *)np.x, (void *)np.v,
-           (void *)np.a, np.n, np.G, np.eps2, np.dt, (long long)iters, s.bpt, s.grid, s.block);
-  std::lock_guard<std::mutex> lk(g_mu);
-  auto it = loop_graphs().find(key);
-  if (it != loop_graphs().end()) {
-    *out = it->second;
-    return MRW_OK;
-  }
+  snprintf(key, sizeof key, "%d|%p|%p|%p|%p|%d|%a|%a|%a|%lld|%d|%d|%d", device, (void *)stream, (void *)np.x,
+           (void *)np.v, (void *)np.a, np.n, np.G, np.eps2, np.dt, (long long)iters, s.bpt, s.grid, s.block);
+  *out = loop_graphs().find(key);
+  if (*out) return MRW_OK;
   LoopGraph g;
   CU(cudaMalloc(&g.ctrl, sizeof(LoopCtrl)));
   cudaError_t e = build_nbody_loop_graph(np, g.ctrl, iters, s.bpt, s.grid, s.block, &g.exec);
@@ -1761,16 +1917,9 @@ mrw_status get_loop_graph(const NBodyParams &np, int64_t iters, const NbShape &s
     cudaFree(g.ctrl);
     return cuda_fail(e, "building the Loop graph");
   }
-  if (loop_graphs().size() > 64) {  // bound the cache: drop everything (waits for the device)
-    cudaDeviceSynchronize();
-    for (auto &kv : loop_graphs()) {
-      cudaGraphExecDestroy(kv.second.exec);
-      cudaFree(kv.second.ctrl);
-    }
-    loop_graphs().clear();
-  }
-  loop_graphs()[key] = g;
-  *out = g;
+  std::shared_ptr<LoopGraph> made;
+  TRY(make_cached(g, destroy_loop_graph, &made));
+  *out = loop_graphs().insert(key, made);
   return MRW_OK;
 }
 
@@ -1821,9 +1970,10 @@ mrw_status enqueue_nbody(Launch &L, const Program &p, const mrw_buffer *args, in
         if (st.from_loop) CU(cudaStreamSynchronize(L.stream));
       }
     } else if (st.from_loop) {
-      LoopGraph g;
-      TRY(get_loop_graph(np, st.iters, s, L.device, &g));
-      CU(cudaGraphLaunch(g.exec, L.stream));
+      std::shared_ptr<LoopGraph> g;
+      TRY(get_loop_graph(np, st.iters, s, L.device, L.stream, &g));
+      RecordOnExit used_until{g->last_use, L.stream};
+      CU(cudaGraphLaunch(g->exec, L.stream));
     } else {
       for (int64_t it = 0; it < st.iters; ++it) {
         CU(launch_nbody_drift(np, L.stream));
@@ -1857,12 +2007,20 @@ mrw_status enqueue_saxpy(Launch &L, const Program &p, const mrw_buffer *args, in
   int64_t pp;
   TRY(resolve(L, vx, true, false, &dx, &pp));
   TRY(resolve(L, vy, true, true, &dy, &pp));
-  const int block = p.wg ? p.wg : (cfg.block ? cfg.block : 256);
-  const int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : 8;
-  const int64_t n = vx.numel();
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)L.sms * cps * std::max(1, 256 / block),
-                                                                (n / 4 + block - 1) / block));
-  for (float a : p.alphas) CU(launch_saxpy((const float *)dx, (float *)dy, n, a, grid, block, L.stream));
+  if (p.wg && p.wg != 256) return fail(MRW_ERR_UNSUPPORTED, "saxpy runs in CTAs of 256 threads");
+  // FUSE_ALL: consecutive stages fused, up to kMaxSaxpyStages per pass over the vectors;
+  // FUSE_NONE: one pass per stage (the kernel-per-stage baseline). unroll: float4 groups per thread.
+  SaxpyArgs a{};
+  a.x = (const float *)dx;
+  a.y = (float *)dy;
+  a.n = vx.numel();
+  const int unroll = cfg.unroll ? cfg.unroll : 4;
+  const size_t per = cfg.fusion == MRW_FUSE_ALL ? (size_t)kMaxSaxpyStages : 1;
+  for (size_t s0 = 0; s0 < p.alphas.size(); s0 += per) {
+    a.nstages = (int32_t)std::min(per, p.alphas.size() - s0);
+    for (int k = 0; k < a.nstages; ++k) a.alpha[k] = p.alphas[s0 + k];
+    CU(launch_saxpy(a, unroll, L.stream));
+  }
   return MRW_OK;
 }
 
@@ -2078,6 +2236,7 @@ void free_future(mrw_future *f) {
   }
   put_sync_events(f->sync_events);
   status_pool().give(f->slot);
+  result_pool().give(f->result_slot);
   delete f;
 }
 
@@ -2242,6 +2401,11 @@ mrw_status replay_chain(const ChainReplay &r, bool timed, mrw_future_t *out) {
     free_future(f);
     return s;
   }
+  if (r.finish_nout > 0) {  // a MapReduce: the result is in the call's args[2] (device memory)
+    f->nresult = r.finish_nout;
+    f->result_src = r.args[2].data;
+    f->result_mem = r.args[2].memory;
+  }
   if (timed) cudaEventRecord(f->start, r.stream);
   cudaError_t e;
   if (r.finish_nout > 0) {
@@ -2279,6 +2443,26 @@ mrw_status execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const
   const uint64_t gen = g_plan_gen.load(std::memory_order_acquire);  // before anything is planned
   Program p;
   TRY(get_program(root, &p));
+  // A MapReduce called without a result buffer: the future owns the result, in a page-locked slot
+  // that the call's work fills (the slot is a host args[2], staged like any host buffer).
+  struct SlotGuard {
+    int64_t *p = nullptr;
+    ~SlotGuard() { result_pool().give(p); }
+  } own_slot;
+  mrw_buffer own[3];
+  if (p.fam == F_IMAGE && p.reduce != RED_NONE && nargs == 2) {
+    TRY(result_pool().take(&own_slot.p));
+    own[0] = args[0];
+    own[1] = args[1];
+    own[2] = mrw_buffer{};
+    own[2].data = own_slot.p;
+    own[2].dtype = MRW_I64;
+    own[2].ndim = 1;
+    own[2].shape[0] = p.reduce == RED_COUNT3 ? 3 : 1;
+    own[2].memory = MRW_MEM_HOST;
+    args = own;
+    nargs = 3;
+  }
   TRY(validate_args(p, args, nargs));
   const mrw_config c = cfg ? *cfg : pick_config(root, p, args, nargs);
   TRY(check_config(c));
@@ -2292,6 +2476,16 @@ mrw_status execute(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const
   if (s != MRW_OK) {
     free_future(f);
     return s;
+  }
+  if (p.fam == F_IMAGE && p.reduce != RED_NONE) {
+    f->nresult = p.reduce == RED_COUNT3 ? 3 : 1;
+    if (own_slot.p) {
+      f->result_slot = own_slot.p;
+      own_slot.p = nullptr;
+    } else {
+      f->result_src = args[2].data;
+      f->result_mem = args[2].memory;
+    }
   }
   if (timed) cudaEventRecord(f->start, L.stream);
   bool used = false;
@@ -2375,6 +2569,37 @@ mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms) {
   return MRW_OK;
 }
 
+mrw_status mrw_future_result(mrw_future_t f, void *host_dst, size_t bytes) {
+  if (!f || !host_dst) return fail(MRW_ERR_INVALID_ARG, "NULL argument");
+  if (f->nresult == 0) return fail(MRW_ERR_INVALID_ARG, "the executed tree has no reduction: the future carries no result");
+  const size_t need = (size_t)f->nresult * sizeof(int64_t);
+  if (bytes < need) return fail(MRW_ERR_INVALID_ARG, "the result takes %zu bytes, the destination has %zu", need, bytes);
+  TRY(mrw_future_wait(f, -1));
+  if (f->result_slot) {
+    memcpy(host_dst, f->result_slot, need);
+  } else if (f->result_mem == MRW_MEM_HOST) {
+    memcpy(host_dst, f->result_src, need);
+  } else {
+    // the call's work has completed, so a copy on a private stream of the future's device reads
+    // the final values; the caller's device is restored afterwards
+    int prev = -1;
+    CU(cudaGetDevice(&prev));
+    if (prev != f->device) CU(cudaSetDevice(f->device));
+    cudaStream_t rs = nullptr;
+    mrw_status st = result_stream(f->device, &rs);
+    cudaError_t e = cudaSuccess;
+    if (st == MRW_OK) {
+      std::lock_guard<std::mutex> lk(g_result_mu);
+      e = cudaMemcpyAsync(host_dst, f->result_src, need, cudaMemcpyDeviceToHost, rs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(rs);
+    }
+    if (prev != f->device) cudaSetDevice(prev);
+    TRY(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the MapReduce result");
+  }
+  return MRW_OK;
+}
+
 void mrw_future_release(mrw_future_t f) {
   if (!f) return;
   cudaEventSynchronize(f->done);  // the status slot must not be reused while a copy is pending
@@ -2394,11 +2619,12 @@ struct BatchPlan {
   unsigned int *counters = nullptr;  // one queue counter per group + a status word
   cudaGraphExec_t exec = nullptr;
   int ngroups = 0;
+  cudaEvent_t last_use = nullptr;  // recorded behind every launch (PlanCache)
 };
 
-std::map<std::string, BatchPlan> &batch_plans() {
-  static std::map<std::string, BatchPlan> m;
-  return m;
+PlanCache<BatchPlan> &batch_plans() {
+  static PlanCache<BatchPlan> *c = new PlanCache<BatchPlan>(32);  // never destroyed: no CUDA calls at exit
+  return *c;
 }
 
 void destroy_batch_plan(BatchPlan &b) {
@@ -2546,7 +2772,8 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
     if (off < 0 || off % 16 || pitch % 16 || pitch < W || pitch > INT32_MAX)
       return fail(MRW_ERR_CONSTRAINT, "instance %lld: offset and pitch must be multiples of 16, pitch >= W",
                   (long long)i);
-    if (off + H * pitch > arena_bytes) return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
+    if (off > arena_bytes || H * pitch > arena_bytes - off)  // H * pitch < 2^51: no overflow
+      return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
   }
   mrw_config c = cfg ? *cfg : default_config(F_IMAGE);
   TRY(check_config(c));
@@ -2558,26 +2785,18 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
            (const void *)in_arena, (void *)out_arena, (long long)arena_bytes, (unsigned long long)dh, (long long)n,
            c.fusion, c.block, c.ctas_per_sm, c.tile_rows, c.tile_cols, c.unroll);
   const std::string key = tree_signature(root) + "|" + keyb;
-  BatchPlan plan;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = batch_plans().find(key);
-    if (it != batch_plans().end()) plan = it->second;
-  }
-  if (!plan.exec) {
-    mrw_status s = build_batch_plan(L, p, in_arena, out_arena, arena_bytes, desc, n, c, &plan);
+  std::shared_ptr<BatchPlan> cached = batch_plans().find(key);
+  if (!cached) {
+    BatchPlan built;
+    mrw_status s = build_batch_plan(L, p, in_arena, out_arena, arena_bytes, desc, n, c, &built);
     if (s != MRW_OK) {
-      destroy_batch_plan(plan);
+      destroy_batch_plan(built);
       return s;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (batch_plans().size() >= 32) {
-      cudaDeviceSynchronize();
-      for (auto &kv : batch_plans()) destroy_batch_plan(kv.second);
-      batch_plans().clear();
-    }
-    batch_plans()[key] = plan;
+    TRY(make_cached(built, destroy_batch_plan, &cached));
+    cached = batch_plans().insert(key, cached);
   }
+  const BatchPlan &plan = *cached;
   mrw_future *f = new (std::nothrow) mrw_future();
   if (!f) return fail(MRW_ERR_OOM, "future");
   f->device = L.device;
@@ -2591,6 +2810,7 @@ mrw_status mrw_execute_batched(mrw_node_t root, const uint8_t *in_arena, uint8_t
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(f->slot.host, plan.counters + plan.ngroups, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                         L.stream);
+  cudaEventRecord(plan.last_use, L.stream);
   f->has_status = true;
   cudaEventRecord(f->done, L.stream);
   if (e != cudaSuccess) {
@@ -2648,8 +2868,9 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
     const ImgGeom geo = geom_of(args[0], vin);
     const std::vector<Group> gs = group_stages(p, c.fusion == MRW_FUSE_ALL, false);
+    const bool chunked = p.while_begin < 0 && chunked_staging(gs, vin, vout, geo);
     o << "{\"family\":\"image\",\"W\":" << geo.W << ",\"H\":" << geo.H << ",\"D\":" << geo.D
-      << ",\"reduce\":" << p.reduce;
+      << ",\"reduce\":" << p.reduce << ",\"staging\":\"" << (chunked ? "chunked" : "whole") << "\"";
     if (p.while_begin >= 0)
       o << ",\"while_changed\":{\"first_stage\":" << p.while_begin << ",\"end_stage\":" << p.while_end
         << ",\"max_iters\":" << p.while_max << ",\"body_kernels\":"
@@ -2688,7 +2909,7 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
           << ",\"nu\":16,\"col_vecs\":" << (geo.W + 15) / 16 << ",\"rows_parallel\":" << s.rows_parallel
           << ",\"grid\":" << s.grid << ",\"block\":" << s.block << ",\"unroll\":" << s.unroll
           << ",\"order\":\"" << (s.blocked ? "blocked" : "persistent") << "\""
-          << ",\"finish_kernel\":" << (g.reduce != RED_NONE ? "true" : "false");
+          << ",\"finish_kernel\":" << (g.reduce != RED_NONE && !chunked ? "true" : "false");
       }
       o << "}";
     }
@@ -2726,7 +2947,13 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     }
     o << "]}";
   } else {
-    o << "{\"family\":\"saxpy\",\"stages\":" << p.alphas.size() << "}";
+    View vx, vy;
+    TRY(validate_saxpy_args(args, nargs, &vx, &vy));
+    const size_t per = c.fusion == MRW_FUSE_ALL ? (size_t)kMaxSaxpyStages : 1;
+    const int unroll = c.unroll ? c.unroll : 4;
+    o << "{\"family\":\"saxpy\",\"n\":" << vx.numel() << ",\"stages\":" << p.alphas.size()
+      << ",\"launches\":" << (p.alphas.size() + per - 1) / per << ",\"unroll\":" << unroll
+      << ",\"block\":256,\"grid\":" << saxpy_grid(vx.numel(), unroll) << "}";
   }
   *out = o.str();
   return MRW_OK;
@@ -3269,7 +3496,17 @@ extern "C" mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t
     if (off < 0 || off % 16 || pitch % 16 || pitch < W || pitch > INT32_MAX)
       return fail(MRW_ERR_CONSTRAINT, "instance %lld: offset and pitch must be multiples of 16, pitch >= W",
                   (long long)i);
-    if (off + H * pitch > arena_bytes) return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
+    // H * pitch < 2^51 cannot overflow; off is compared on its own first
+    if (off > arena_bytes || H * pitch > arena_bytes - off)
+      return fail(MRW_ERR_SHAPE, "instance %lld lies outside the arena", (long long)i);
+  }
+  {
+    // a captured call would leave graph nodes that read the shared host staging tables when the
+    // graph is replayed, after later calls have overwritten them
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(MRW_ERR_UNSUPPORTED, "the allocation-free batched call cannot be captured into a CUDA graph");
   }
   mrw_config c = cfg ? *cfg : default_config(F_IMAGE);
   TRY(check_config(c));
@@ -3302,5 +3539,111 @@ extern "C" mrw_status mrw_execute_batched_noalloc(mrw_node_t root, const uint8_t
   const cudaError_t e =
       launch_stencil_noalloc(a, in_arena, out_arena, desc, n, sms, s.cps, s.smem, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "allocation-free batched launch");
+  return MRW_OK;
+}
+
+extern "C" mrw_status mrw_noalloc_status(void *stream, uint32_t *host_status) {
+  if (!host_status) return fail(MRW_ERR_INVALID_ARG, "host_status is NULL");
+  unsigned int v = 0;
+  const cudaError_t e = stencil_noalloc_status((cudaStream_t)stream, &v);
+  if (e != cudaSuccess) return cuda_fail(e, "status of the allocation-free batched call");
+  *host_status = v;
+  if (v) return fail(MRW_ERR_DEVICE, "the last allocation-free batched call gave up a tile wait (status %u)", v);
+  return MRW_OK;
+}
+
+// ============================================================================================
+// CPU + GPU co-execution of a pointwise image tree (Section 3.3; the balancer is in coexec.cpp)
+// ============================================================================================
+namespace mrw {
+mrw_status report_error(mrw_status s, const char *msg) {
+  t_err = msg;
+  return s;
+}
+}  // namespace mrw
+
+extern "C" mrw_status mrw_execute_coexec(mrw_balancer_t b, mrw_node_t root, const mrw_buffer *args, int32_t nargs,
+                                         const mrw_config *cfg, void *stream, mrw_balance_report *rep) {
+  if (!b) return fail(MRW_ERR_INVALID_ARG, "balancer is NULL");
+  if (nargs < 0 || (nargs && !args)) return fail(MRW_ERR_INVALID_ARG, "bad argument list");
+  Program p;
+  TRY(get_program(root, &p));
+  if (p.fam != F_IMAGE || p.while_begin >= 0)
+    return fail(MRW_ERR_UNSUPPORTED, "co-execution runs image trees without WHILE_CHANGED loops");
+  if (nargs < 2 || args[0].memory != MRW_MEM_HOST || args[1].memory != MRW_MEM_HOST)
+    return fail(MRW_ERR_UNSUPPORTED, "co-execution shares host image buffers between the GPU and the host cores");
+  View vin, vout, vred;
+  TRY(validate_image_args(p, args, nargs, &vin, &vout, &vred));
+  const std::vector<Group> gs = group_stages(p, true, false);
+  if (gs.size() != 1 || gs[0].use_stencil || gs[0].user || gs[0].reduce_only)
+    return fail(MRW_ERR_UNSUPPORTED, "co-execution runs trees that fuse into one pointwise kernel");
+  if (cfg) TRY(check_config(*cfg));
+  HostChainOp ops[MRW_MAX_STAGES];
+  int nops = 0;
+  for (const ImgStage &s : p.img) {
+    if (s.kind != OP_NOISE && s.kind != OP_SOLARISE && s.kind != OP_MIRROR && s.kind != OP_THRESH)
+      return fail(MRW_ERR_UNSUPPORTED, "co-execution runs the built-in pointwise stages");
+    ops[nops++] = HostChainOp{s.kind, s.seed, s.t};
+  }
+  const ImgGeom geo = geom_of(args[0], vin);
+  std::lock_guard<std::mutex> lk(balancer_mutex(b));  // one co-executed run at a time per balancer
+  const double share = balancer_share_locked(b);
+  const int64_t gr = std::min<int64_t>(geo.rows, std::max<int64_t>(0, std::llround(share * (double)geo.rows)));
+  const int64_t cr = geo.rows - gr;
+  // the GPU's share: the first gr rows, as a (gr, W) image over the same host rows (the noise hash's
+  // rows are global, and these are rows 0 .. gr-1); its MapReduce result stays in its future
+  mrw_future_t fut = nullptr;
+  if (gr > 0) {
+    mrw_buffer sub[2] = {args[0], args[1]};
+    const View *vv[2] = {&vin, &vout};
+    for (int k = 0; k < 2; ++k) {
+      sub[k].ndim = 2;
+      sub[k].shape[0] = gr;
+      sub[k].shape[1] = geo.W;
+      sub[k].shape[2] = sub[k].shape[3] = 0;
+      sub[k].pitch = vv[k]->pitch;
+      sub[k].epu = 0;
+    }
+    TRY(execute(root, sub, 2, cfg, stream, &fut, true));
+  }
+  // the host threads' share, at the same time: rows gr .. rows-1
+  const auto t0 = std::chrono::steady_clock::now();
+  uint64_t cpu_red[3] = {0, 0, 0};
+  if (cr > 0) {
+    const mrw_status s = balancer_run_host_share(b, ops, nops, (const uint8_t *)args[0].data + gr * vin.pitch,
+                                                 vin.pitch, (uint8_t *)args[1].data + gr * vout.pitch, vout.pitch,
+                                                 (int)geo.W, gr, cr, p.reduce);
+    if (s == MRW_OK) balancer_wait_host_share(b, cpu_red);
+  }
+  const double cpu_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  double gpu_ms = 0.0;
+  int64_t gpu_red[3] = {0, 0, 0};
+  if (fut) {
+    mrw_status s = mrw_future_wait(fut, -1);
+    float ms = 0.f;
+    if (s == MRW_OK) s = mrw_future_elapsed_ms(fut, &ms);
+    if (s == MRW_OK && p.reduce != RED_NONE)
+      s = mrw_future_result(fut, gpu_red, sizeof(int64_t) * (p.reduce == RED_COUNT3 ? 3 : 1));
+    const std::string msg = t_err;
+    mrw_future_release(fut);
+    if (s != MRW_OK) return fail(s, "%s", msg.c_str());
+    gpu_ms = ms;
+  }
+  if (p.reduce != RED_NONE) {  // merging function + of the two partial results (Section 3.4)
+    const int k = p.reduce == RED_COUNT3 ? 3 : 1;
+    int64_t total[3];
+    for (int i = 0; i < k; ++i) total[i] = gpu_red[i] + (int64_t)cpu_red[i];
+    if (args[2].memory == MRW_MEM_HOST) {
+      memcpy(args[2].data, total, sizeof(int64_t) * k);
+    } else {
+      CU(cudaMemcpyAsync(args[2].data, total, sizeof(int64_t) * k, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+      CU(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+  }
+  mrw_balance_report r{};
+  balancer_observe_locked(b, gpu_ms, cpu_ms, &r);
+  r.gpu_rows = gr;
+  r.cpu_rows = cr;
+  if (rep) *rep = r;
   return MRW_OK;
 }

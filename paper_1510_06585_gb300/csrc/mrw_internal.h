@@ -6,7 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+
+#include "mrw.h"
 
 namespace mrw {
 
@@ -179,6 +182,9 @@ constexpr int kNoAllocMaxInstances = 256;
 size_t stencil_noalloc_scratch_bytes();
 cudaError_t launch_stencil_noalloc(StencilArgs a, const uint8_t *in_base, uint8_t *out_base, const int64_t *desc,
                                    int64_t n, int sms, int cps, size_t smem, cudaStream_t s);
+// The status word of the allocation-free launch's array, read on stream `s` after the work enqueued
+// before it (0: every tile wait of the last launch ended in time).
+cudaError_t stencil_noalloc_status(cudaStream_t s, unsigned int *out);
 // Encode a 3-D u8 tensor map for `base` with the stencil box of the given tile shape.
 cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t H, int64_t D, int64_t pitch,
                           int box_w, int box_h);
@@ -228,7 +234,19 @@ cudaError_t build_nbody_loop_graph(const NBodyParams &p, LoopCtrl *ctrl, int64_t
 // ------------------------------------------------------------------------------------------
 // SAXPY and helpers
 // ------------------------------------------------------------------------------------------
-cudaError_t launch_saxpy(const float *x, float *y, int64_t n, float alpha, int grid, int block, cudaStream_t s);
+// A Map of nstages saxpy stages fused into one pass: y := alpha[s] x + y for s in order (one fmaf per
+// stage and element). x, y 16-byte aligned, n elements; unroll in {1, 2, 4, 8} float4 groups per
+// thread (CTAs of 256 threads, one per 256 * unroll groups).
+constexpr int kMaxSaxpyStages = 64;
+struct SaxpyArgs {
+  const float *x;
+  float *y;
+  int64_t n;
+  int32_t nstages;
+  float alpha[kMaxSaxpyStages];
+};
+cudaError_t launch_saxpy(const SaxpyArgs &a, int unroll, cudaStream_t s);
+int saxpy_grid(int64_t n, int unroll);
 cudaError_t launch_fill_u32(unsigned int *p, unsigned int v, int64_t n, cudaStream_t s);
 
 // WHILE_CHANGED loops: a := b where they differ and *changed := 1 if any byte differed; the
@@ -266,6 +284,31 @@ bool jit_check(const std::string &src, int arch, std::string *err);
 // device for the life of the process); false with a message in *err.
 bool jit_kernel(const std::string &src, const char *entry, int device, int arch, cudaKernel_t *kernel,
                 std::string *err);
+
+// ------------------------------------------------------------------------------------------
+// CPU + GPU co-execution (coexec.cpp)
+// ------------------------------------------------------------------------------------------
+// Sets this thread's mrw_last_error message and returns s.
+mrw_status report_error(mrw_status s, const char *msg);
+// One pointwise stage of the host workers' share (kind: OP_NOISE, OP_SOLARISE, OP_MIRROR, OP_THRESH).
+struct HostChainOp {
+  int32_t kind;
+  uint32_t seed;
+  uint32_t t;  // OP_THRESH thresholds, t0 | t1 << 8
+};
+// Rows [r0, r1) of an image through the stages, one row at a time (row r has global index y0 + r);
+// red3 receives the rows' class counts (RED_COUNT3) or value sum in red3[0] (RED_SUM).
+void host_chain_rows(const HostChainOp *ops, int nops, const uint8_t *in, int64_t in_pitch, uint8_t *out,
+                     int64_t out_pitch, int W, int64_t y0, int64_t r0, int64_t r1, int reduce, uint64_t *red3);
+// The balancer's host side: start the host share on its worker threads (returns at once), wait for
+// it and merge its partial results; the share, lock and bookkeeping of a run.
+mrw_status balancer_run_host_share(mrw_balancer *b, const HostChainOp *ops, int nops, const uint8_t *in,
+                                   int64_t in_pitch, uint8_t *out, int64_t out_pitch, int W, int64_t y0,
+                                   int64_t rows, int reduce);
+void balancer_wait_host_share(mrw_balancer *b, uint64_t *red3);
+double balancer_share_locked(mrw_balancer *b);
+std::mutex &balancer_mutex(mrw_balancer *b);
+void balancer_observe_locked(mrw_balancer *b, double gpu_ms, double cpu_ms, mrw_balance_report *rep);
 
 // ------------------------------------------------------------------------------------------
 // Cost-model MLP (bf16 weights, fp32 accumulation)

@@ -57,6 +57,24 @@ class mrw_config(ctypes.Structure):
         return (self.fusion, self.block, self.ctas_per_sm, self.tile_rows, self.tile_cols, self.unroll)
 
 
+class mrw_balance_params(ctypes.Structure):
+    _fields_ = [("weight", ctypes.c_double), ("max_dev", ctypes.c_double), ("c_factor", ctypes.c_double),
+                ("trigger", ctypes.c_double), ("precision", ctypes.c_double), ("gpu_share", ctypes.c_double),
+                ("cpu_threads", ctypes.c_int32), ("search_reps", ctypes.c_int32)]
+
+
+class mrw_balance_report(ctypes.Structure):
+    _fields_ = [("gpu_share", ctypes.c_double), ("gpu_rows", ctypes.c_int64), ("cpu_rows", ctypes.c_int64),
+                ("gpu_ms", ctypes.c_double), ("cpu_ms", ctypes.c_double), ("dev", ctypes.c_double),
+                ("unbalanced", ctypes.c_int32), ("phase", ctypes.c_int32), ("lbt", ctypes.c_double),
+                ("next_share", ctypes.c_double), ("transferable", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+MRW_BAL_SEARCH, MRW_BAL_MONITOR, MRW_BAL_SHIFT, MRW_BAL_BISECT = range(4)
+
 _P = ctypes.c_void_p
 _SIGS = {
     "mrw_abi_version": (ctypes.c_int32, []),
@@ -81,9 +99,11 @@ _SIGS = {
                                            ctypes.POINTER(mrw_config), _P, ctypes.POINTER(_P)]),
     "mrw_execute_batched_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                                    ctypes.c_int64, ctypes.POINTER(mrw_config), _P]),
+    "mrw_noalloc_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "mrw_future_wait": (ctypes.c_int, [_P, ctypes.c_int64]),
     "mrw_future_query": (ctypes.c_int, [_P]),
     "mrw_future_elapsed_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "mrw_future_result": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "mrw_future_release": (None, [_P]),
     "mrw_plan_describe": (ctypes.c_int, [_P, ctypes.POINTER(mrw_buffer), ctypes.c_int32, ctypes.POINTER(mrw_config),
                                          ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -109,6 +129,12 @@ _SIGS = {
     "mrw_model_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                        ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_float)]),
     "mrw_tune_set_model": (ctypes.c_int, [_P, ctypes.POINTER(mrw_config), ctypes.c_int32]),
+    "mrw_balancer_create": (ctypes.c_int, [ctypes.POINTER(mrw_balance_params), ctypes.POINTER(_P)]),
+    "mrw_balancer_release": (None, [_P]),
+    "mrw_balancer_observe": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(mrw_balance_report)]),
+    "mrw_balancer_share": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "mrw_execute_coexec": (ctypes.c_int, [_P, _P, ctypes.POINTER(mrw_buffer), ctypes.c_int32,
+                                          ctypes.POINTER(mrw_config), _P, ctypes.POINTER(mrw_balance_report)]),
 }
 
 _lib = None
@@ -310,6 +336,13 @@ class Future:
     def wait(self, timeout_ms: int = -1) -> None:
         check(load().mrw_future_wait(self.h, timeout_ms), "mrw_future_wait")
 
+    def result(self, n: int = 3):
+        """mrw_future_result: the MapReduce result (n int64 values) as a numpy array."""
+        import numpy as np
+        out = np.zeros(n, dtype=np.int64)
+        check(load().mrw_future_result(self.h, out.ctypes.data, out.nbytes), "mrw_future_result")
+        return out
+
     def elapsed_ms(self) -> float:
         v = ctypes.c_float()
         check(load().mrw_future_elapsed_ms(self.h, ctypes.byref(v)), "mrw_future_elapsed_ms")
@@ -471,3 +504,39 @@ def unpack_params(flat, k: int, hidden: int = 64, nin: int = MRW_NFEATURES) -> d
 def pack_params(p: dict):
     import numpy as np
     return np.concatenate([np.asarray(p[k], np.float32).reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+class Balancer:
+    """Owning handle of an mrw_balancer_t (CPU + GPU co-execution with dynamic load balancing)."""
+
+    def __init__(self, weight=0.0, max_dev=0.0, c_factor=0.0, trigger=0.0, precision=0.0, gpu_share=-1.0,
+                 cpu_threads=0, search_reps=0):
+        p = mrw_balance_params()
+        p.weight, p.max_dev, p.c_factor, p.trigger, p.precision = weight, max_dev, c_factor, trigger, precision
+        p.gpu_share, p.cpu_threads, p.search_reps = gpu_share, cpu_threads, search_reps
+        self.h = ctypes.c_void_p()
+        check(load().mrw_balancer_create(ctypes.byref(p), ctypes.byref(self.h)), "mrw_balancer_create")
+
+    def observe(self, gpu_ms: float, cpu_ms: float) -> dict:
+        r = mrw_balance_report()
+        check(load().mrw_balancer_observe(self.h, gpu_ms, cpu_ms, ctypes.byref(r)), "mrw_balancer_observe")
+        return r.as_dict()
+
+    def share(self) -> float:
+        v = ctypes.c_double()
+        check(load().mrw_balancer_share(self.h, ctypes.byref(v)), "mrw_balancer_share")
+        return v.value
+
+    def execute(self, root: Node, args, cfg: mrw_config | None = None, stream=None) -> dict:
+        """mrw_execute_coexec: blocking; returns the run's balance report."""
+        arr = buffers(*args)
+        r = mrw_balance_report()
+        st = stream_handle(stream) if stream is not None or _cuda_available() else None
+        check(load().mrw_execute_coexec(self.h, root.h, arr, len(args), ctypes.byref(cfg) if cfg is not None else None,
+                                        st, ctypes.byref(r)), "mrw_execute_coexec")
+        return r.as_dict()
+
+    def __del__(self):
+        if _lib is not None and self.h:
+            _lib.mrw_balancer_release(self.h)
+            self.h = ctypes.c_void_p()

@@ -149,6 +149,11 @@ def test_mapreduce_fuses_into_the_last_chain_group(lib):
     assert (g_red["grid"], g_red["block"], g_red["rows_parallel"]) == (g_map["grid"], g_map["block"],
                                                                        g_map["rows_parallel"])
     assert g_red["grid"] * g_red["block"] == g_red["rows_parallel"] * g_red["col_vecs"] and g_red["order"] == "blocked"
+    # pageable host buffers of 8 MiB and more are staged in overlapped chunks whose kernels add into
+    # the zeroed result: no finish kernel; below that size the whole image is staged and finished
+    assert d["staging"] == "whole"
+    chunked = mrw.plan_describe(mr, big, cfg)
+    assert chunked["staging"] == "chunked" and chunked["groups"][0]["finish_kernel"] is False
 
 
 def test_loops_of_image_stages_unroll_into_the_chain(lib):
@@ -270,3 +275,18 @@ def test_blur_prefix_sequences(lib):
     d = mrw.plan_describe(mrw.pipeline(mrw.stage("solarise"), mrw.stage("noise", seed=1), mrw.stage("blur5"),
                                        mrw.stage("solarise")), _image_args(300, 333))["groups"]
     assert d[0]["kernel"] == "stencil" and d[0]["pre_pattern"] == "generic"
+
+
+def test_future_result_rejects_null_arguments(lib):
+    out = np.zeros(3, dtype=np.int64)
+    assert lib.mrw_future_result(None, out.ctypes.data, out.nbytes) == mrw.MRW_ERR_INVALID_ARG
+
+
+def test_saxpy_stages_fuse_into_passes_of_64(lib):
+    x = np.zeros(1000, np.float32)
+    y = np.zeros(1000, np.float32)
+    tree = mrw.loop(mrw.stage("saxpy", alpha=0.5), 100)
+    d = mrw.plan_describe(tree, [x, y])
+    assert d["family"] == "saxpy" and d["stages"] == 100 and d["launches"] == 2 and d["n"] == 1000
+    assert mrw.plan_describe(tree, [x, y], mrw.config(fusion=mrw.MRW_FUSE_NONE))["launches"] == 100
+    assert mrw.plan_describe(tree, [x, y], mrw.config(unroll=8))["grid"] == 1

@@ -11,12 +11,15 @@ from paper_1510_06585_gb300 import mrw as M
 pytestmark = pytest.mark.gpu
 
 
-def test_learned_choices_beat_the_default_configuration():
-    res, model, std = C.experiment(n_train=1200, n_test=200, max_log2=22, epochs=150, reps=2, log=None)
-    learned, default = res["learned"], res["default_config"]
-    assert learned["mean"] < default["mean"], res
-    assert learned["mean"] <= res["random_config"]["mean"], res
-    assert learned["mean"] <= 0.35, res
+def test_learned_choices_come_within_ten_percent_and_beat_nearest_neighbour():
+    # 4000 training and 500 unseen random skeletons of up to 2^26 elements, every one of the 16
+    # candidate configurations timed by the exhaustive tuner
+    res, model, std = C.experiment(n_train=4000, n_test=500, max_log2=26, epochs=300, reps=3, log=None)
+    learned, default, nn = res["learned"], res["default_config"], res["nearest_neighbour_kb"]
+    print({k: res[k] for k in ("learned", "nearest_neighbour_kb", "default_config")})
+    assert learned["mean"] <= 0.10, res  # the workload's target: within 10 % of the tuner's best
+    assert learned["mean"] < nn["mean"], res  # the paper's derivation above 3 dimensions (Section 3.2)
+    assert learned["mean"] < default["mean"] and learned["mean"] < res["random_config"]["mean"], res
     assert res["final_train_loss"] < 1.0, res
 
 

@@ -91,14 +91,3 @@ print("after", int(y.sum().item()) > 0)
     assert r.returncode == 0, r.stderr
     assert "status %d" % M.MRW_ERR_DEVICE in r.stdout, r.stdout
     assert "after True" in r.stdout, r.stdout
-
-
-def test_saxpy_map():
-    n = 1_000_003
-    rng = np.random.Generator(np.random.PCG64(2))
-    x = rng.normal(size=n).astype(np.float32)
-    y = rng.normal(size=n).astype(np.float32)
-    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    M.execute(M.map_(M.stage("saxpy", alpha=2.5)), [xd, yd]).wait(60000)
-    want = 2.5 * x.astype(np.float64) + y
-    assert np.abs(yd.cpu().numpy() - want).max() <= 1e-6 * np.abs(want).max()
