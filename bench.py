@@ -6,9 +6,12 @@ Headline workload (one "step" = one execution of the skeleton on one input):
   into 3 classes written as uint8 labels, the MapReduce (+) produces int64 class counts (Section 4
   of the paper, Segmentation). Algorithmic bytes per step: 128 MiB read + 128 MiB written + 24 B.
   value = fused skeleton GB/s over all ranks; the kernel-per-stage version is timed beside it.
-Also measured in the same run (keys under "workloads"): the Filter Pipeline on 1024^2 and 8192^2,
-N-body (65536 bodies, 100 Loop iterations, GFLOP/s at 20 flop per interaction), and the batched
-4096-instance Filter Pipeline + 5x5 blur; each fused and kernel-per-stage.
+Also measured in the same run (keys under "workloads"): the Filter Pipeline on 1024^2 .. 16384^2,
+N-body (65536 bodies, 100 Loop iterations, GFLOP/s at 20 flop per interaction), the batched
+4096-instance Filter Pipeline + 5x5 blur, FFT pipelined with its inversion, the Saxpy Map and the
+learned cost model; each fused and kernel-per-stage. After its timed loops every workload checks
+the bytes it timed against the oracle ("checked"), reports its roofline and the oracle timed on
+the host's cores ("cpu_baseline").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrw|reference] [--no-extras]
 Under torchrun each rank runs its own replica on its own GPU (weak scaling, no collective on the
@@ -231,7 +234,8 @@ def run_mrw(args):
             pending.clear()
 
         out = extras(M, lib, device, world, torch.cuda.current_stream().cuda_stream, peaks, pending, drain_only,
-                     set(args.workloads.split(",")), args.batch_n, args.filter_sides)
+                     set(args.workloads.split(",")), args.batch_n, args.filter_sides, tune=args.tune,
+                     cpu=args.cpu_baseline)
         if rank == 0:
             print(json.dumps({"workloads": out}), flush=True)
         return
@@ -286,10 +290,17 @@ def run_mrw(args):
     t_fused = time_steps(step_async(fused_cfg), K, W, world, device, sampler)
     host_enqueue_us = time_steps.host_enqueue_us  # host time to enqueue one step (no GPU wait inside)
     drain()
-    # correctness of what was timed
-    hist = np.bincount(np.digitize(vol.reshape(-1), [85, 170]), minlength=3).astype(np.int64)
-    for x, y, c in sets:
-        assert np.array_equal(c.cpu().numpy(), hist), "segmentation counts differ from the histogram"
+    # the bytes that were timed: every label of both output sets and their counts, against the
+    # oracle's Map and MapReduce (in blocks of 32 planes)
+    from oracle import image as OI
+    want_counts = np.zeros(3, dtype=np.int64)
+    want_labels = np.empty_like(vol)
+    for z in range(0, SEG_SHAPE[0], 32):
+        want_labels[z:z + 32], cnt = OI.segmentation(vol[z:z + 32])
+        want_counts += cnt
+    seg_checked = all(np.array_equal(y.cpu().numpy(), want_labels) and np.array_equal(c.cpu().numpy(), want_counts)
+                      for _, y, c in sets)
+    hist = want_counts
     t_unfused = time_steps(step_async(unfused_cfg), K, W, world, device)
     drain()
     # the same bytes moved by a plain device copy (torch's copy kernel, 128 MiB read + 128 MiB
@@ -325,9 +336,44 @@ def run_mrw(args):
     e2e_cfg = e2e_cands[int(np.argmin(e2e_t))]
     k_e2e = max(1, min(K, 50))
     t_e2e = time_steps(e2e_with(e2e_cfg), k_e2e, min(W, 3), world, device)
-    drain()
-    assert np.array_equal(hc.numpy(), hist)
     e2e_value = world * SEG_BYTES * k_e2e / t_e2e / 1e9
+    drain()
+    e2e_checked = bool(np.array_equal(hc.numpy(), hist) and np.array_equal(hy.numpy(), want_labels))
+
+    # ---------------- CPU + GPU co-execution on the same host buffers (Section 3.3) ----------------
+    # the balancer's profile construction (a binary search on the GPU's share of the rows) from an
+    # even split, then timed runs at the share it settled on, each run blocking until both shares
+    # are done; every run's labels and counts against the oracle
+    coexec = None
+    if args.coexec:
+        M.Balancer(gpu_share=0.5).execute(tree, [hx, hy, hc])  # first-touch costs, outside the search
+        bal = M.Balancer(precision=1.0 / 128, search_reps=2)
+        trace, co_checked = [], True
+        for _ in range(24):
+            r = bal.execute(tree, [hx, hy, hc])
+            trace.append(r)
+            if r["phase"] == M.MRW_BAL_MONITOR:
+                break
+        co_checked = bool(np.array_equal(hc.numpy(), hist) and np.array_equal(hy.numpy(), want_labels))
+        k_co = max(1, min(K, 20))
+        t0 = time.perf_counter()
+        runs = [bal.execute(tree, [hx, hy, hc]) for _ in range(k_co)]
+        t_co = time.perf_counter() - t0
+        co_checked = co_checked and bool(np.array_equal(hc.numpy(), hist) and np.array_equal(hy.numpy(), want_labels))
+        coexec = {"value": round(world * SEG_BYTES * k_co / t_co / 1e9, 2), "unit": "GB/s", "steps": k_co,
+                  "gpu_share": round(runs[-1]["gpu_share"], 5), "gpu_ms": round(float(np.median([x["gpu_ms"] for x in runs])), 3),
+                  "cpu_ms": round(float(np.median([x["cpu_ms"] for x in runs])), 3),
+                  "dev": round(float(np.median([x["dev"] for x in runs])), 4), "lbt": round(runs[-1]["lbt"], 4),
+                  "unbalanced_runs": int(sum(x["unbalanced"] for x in runs)),
+                  "cpu_threads": host_cores(), "gpu_only_e2e_gbs": round(e2e_value, 2),
+                  "speedup_over_gpu_only": round(world * SEG_BYTES * k_co / t_co / 1e9 / e2e_value, 3),
+                  "search_trace": [[round(x["gpu_share"], 5), round(x["gpu_ms"], 3), round(x["cpu_ms"], 3),
+                                    round(x["dev"], 4), round(x["lbt"], 4), x["phase"]] for x in trace],
+                  "trace_columns": ["gpu_share", "gpu_ms", "cpu_ms", "dev", "lbt", "phase"],
+                  "checked": co_checked,
+                  "note": "pinned host buffers; the GPU reads and writes its rows in place over NVLink-C2C, the host "
+                          "threads compute the remaining rows; blocking runs, wall-clock timed"}
+    del want_labels
 
     # what the host link carries: the copy engines moving the same bytes both ways at once (the
     # input to the device on one stream, the device labels back on another), 128 MiB each way
@@ -369,9 +415,12 @@ def run_mrw(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
                 "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e,
                 "host_link_copy_gbs": round(link_gbs, 2), "frac_of_host_link": round(e2e_value / link_gbs, 4),
-                "cfg": list(e2e_cfg.as_tuple()),
+                "cfg": list(e2e_cfg.as_tuple()), "checked": e2e_checked,
                 "note": "pinned host buffers read and written in place over NVLink-C2C by the fused kernel; "
                         "host_link_copy_gbs = the copy engines moving the same bytes both ways at once"},
+        "checked": bool(seg_checked),
+        "check": "all 512^3 labels of both rotating output sets and their class counts against the oracle",
+        "coexec": coexec,
         "gpu_launches": K * launches_per_step,
         "host_enqueue_us_per_step": round(host_enqueue_us, 2),
         "clocks": sampler.summary(),
@@ -379,11 +428,13 @@ def run_mrw(args):
 
     # ---------------- other workloads of the hot path ----------------
     if args.extras:
+        clk = result["clocks"].get("sm_mhz") or 2070.0
         result["workloads"] = extras(M, lib, device, world, stream, peaks, pending, drain,
-                                     set(args.workloads.split(",")), args.batch_n, args.filter_sides)
+                                     set(args.workloads.split(",")), args.batch_n, args.filter_sides,
+                                     tune=args.tune, sm_mhz=clk, cpu=args.cpu_baseline and rank == 0)
 
     # ---------------- CPU baseline (oracle) ----------------
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(vol)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -412,7 +463,76 @@ def tune_candidates_buffers(M, tree, bufarr, reps=5):
                                 "default_ms": round(float(t[0]), 5), "best_ms": round(float(t[bf]), 5)}
 
 
-def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n, filter_sides="1024,4096,8192,16384"):
+# --------------------------------------------------------------------------------------------
+# the oracle on the host's cores (CPU baselines) and the recorded pipe counters (ALU rooflines)
+# --------------------------------------------------------------------------------------------
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(jobs, units_per_rep, unit, sample, min_seconds=2.0, threads=None, scale=1.0, extra=None):
+    """Time the list of oracle calls `jobs` (each a zero-argument callable) on `threads` host
+    threads, repeated for at least min_seconds; numpy releases the interpreter lock inside its
+    array loops, so the threads run on separate cores. Returns the cpu_baseline record:
+    units_per_rep * scale per rep / seconds."""
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or host_cores()
+    reps = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        while True:
+            list(ex.map(lambda f: f(), jobs))
+            reps += 1
+            dt = time.perf_counter() - t0
+            if dt >= min_seconds:
+                break
+    rec = {"value": round(units_per_rep * scale * reps / dt, 4), "unit": unit, "cores": min(threads, len(jobs)),
+           "kind": "oracle", "sample": f"{reps} x {sample}", "seconds": round(dt, 2)}
+    if extra:
+        rec.update(extra)
+    return rec
+
+
+def recorded_pipes(kernel_src: str, key: str):
+    """Per-unit pipe instruction counts of a kernel from the committed ncu summary
+    (profiles/pipes.json), if the kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "pipes.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(key)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1510_06585_gb300", "csrc", kernel_src)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec if rec.get("source_sha256_16") == h else None
+
+
+def alu_roofline(units_per_s, pipes, sm_mhz, sms=152):
+    """Integer-ALU roofline of a kernel that the ALU pipe bounds, from its recorded pipe counters:
+    the ALU pipe retires 64 lanes per SM per clock, so the unit rate cannot exceed
+    sms * 64 * f / (ALU thread-instructions per unit). Beside it: the FMA-heavy pipe (integer
+    multiplies, 64 lanes per SM per clock; the recorded figure counts a multiply-high twice) and
+    the issue slots (4 warp-instructions, 128 lanes, per SM per clock) for all instructions."""
+    if not pipes:
+        return {"bound": "alu", "frac": None, "note": "no pipe counters recorded for this kernel source"}
+    f = sm_mhz * 1e6
+    alu_peak = sms * 64 * f / pipes["alu_per_unit"]
+    fma_peak = sms * 64 * f / pipes["fma_per_unit"]
+    issue_peak = sms * 128 * f / pipes["issue_per_unit"]
+    return {"bound": "alu", "frac": round(units_per_s / alu_peak, 4), "achieved_units_per_s": round(units_per_s, 1),
+            "peak_units_per_s": round(alu_peak, 1), "unit": pipes["unit"], "clock_mhz": sm_mhz,
+            "frac_fma_pipe": round(units_per_s / fma_peak, 4), "frac_issue": round(units_per_s / issue_peak, 4),
+            "alu_per_unit": pipes["alu_per_unit"], "fma_per_unit": pipes["fma_per_unit"],
+            "issue_per_unit": pipes["issue_per_unit"],
+            "peak_source": "derived from the recorded ncu pipe counters (profiles/" + pipes["summary"] + ")"}
+
+
+def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n, filter_sides="1024,4096,8192,16384",
+           tune=True, sm_mhz=2070.0, cpu=True):
     import torch
 
     from paper_1510_06585_gb300 import inputs
@@ -443,61 +563,181 @@ def extras(M, lib, device, world, stream, peaks, pending, drain, which, batch_n,
             pending.append(fut)
         return f
 
-    fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
-    # Filter Pipeline (noise -> solarise -> mirror)
-    ftree = M.pipeline(M.stage("noise", seed=2), M.stage("solarise"), M.stage("mirror"))
-    sides = [int(v) for v in filter_sides.split(",") if v] if "filter" in which else []
-    # sides up to 2048 are L2-resident (reported as latency); above, enough rotating input/output
-    # sets that consecutive steps touch at least 512 MiB (about 4x L2), at least two sets
-    for side, nsets in ((v, 1 if v <= 2048 else max(2, -(-(512 << 20) // (2 * v * v)))) for v in sides):
-        img = inputs.filter_image(side, side)
-        sets = []
-        for _ in range(nsets):
-            x = torch.from_numpy(img).to(device)
-            sets.append(M.buffers(x, torch.empty_like(x)))
-        reps = 200 if side == 1024 else 20
-        f_cfg, u_cfg, tinfo = tune_candidates_buffers(M, ftree, sets[0])
-        tf = timed(launcher(ftree, sets, f_cfg), reps)
-        tu = timed(launcher(ftree, sets, u_cfg), reps)
-        b = 2 * side * side
-        out[f"filter_{side}"] = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2), "tuned": tinfo,
-                                 "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
-                                 "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
-                                 "l2": (f"resident ({b >> 20} MiB)" if nsets == 1 and side <= 2048 else
-                                        f"{nsets} rotating sets, {nsets * b >> 20} MiB")}
+    ctx = {"M": M, "lib": lib, "device": device, "timed": timed, "launcher": launcher, "peaks": peaks,
+           "pending": pending, "drain": drain, "stream": stream, "tune": tune, "sm_mhz": sm_mhz, "cpu": cpu}
+    if "filter" in which:
+        out.update(filter_workload(ctx, [int(v) for v in filter_sides.split(",") if v]))
     if "nbody" in which:
-        out.update(nbody_workload(M, device, timed, launcher, fused, unfused))
+        out.update(nbody_workload(ctx))
     if "batched" in which:
-        out.update(batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n))
+        out.update(batched_workload(ctx, batch_n))
     if "fft" in which:
-        out.update(fft_workload(M, device, timed, launcher, fused, unfused, peaks))
+        out.update(fft_workload(ctx))
+    if "saxpy" in which:
+        out.update(saxpy_workload(ctx))
     if "costmodel" in which:
         out.update(costmodel_workload())
     return out
 
 
-def fft_workload(M, device, timed, launcher, fused, unfused, peaks, nfft=256):
+def filter_workload(ctx, sides):
+    """Filter Pipeline (noise -> solarise -> mirror) on side x side u8 images (Section 4)."""
+    import torch
+
+    from oracle import image as O
+    from paper_1510_06585_gb300 import inputs
+    M, timed, launcher, peaks = ctx["M"], ctx["timed"], ctx["launcher"], ctx["peaks"]
+    out = {}
+    seed = 2
+    ftree = M.pipeline(M.stage("noise", seed=seed), M.stage("solarise"), M.stage("mirror"))
+    pipes = recorded_pipes("k_chain.cu", "filter_chain")
+    # sides up to 2048 are L2-resident (reported as latency); above, enough rotating input/output
+    # sets that consecutive steps touch at least 512 MiB (about 4x L2), at least two sets
+    for side in sides:
+        nsets = 1 if side <= 2048 else max(2, -(-(512 << 20) // (2 * side * side)))
+        img = inputs.filter_image(side, side)
+        sets, ins, outs = [], [], []  # the tensors stay referenced: the descriptors hold raw pointers
+        for _ in range(nsets):
+            x = torch.from_numpy(img).to(ctx["device"])
+            y = torch.empty_like(x)
+            ins.append(x)
+            outs.append(y)
+            sets.append(M.buffers(x, y))
+        reps = 200 if side == 1024 else 20
+        if ctx["tune"]:
+            f_cfg, u_cfg, tinfo = tune_candidates_buffers(M, ftree, sets[0])
+        else:
+            f_cfg, u_cfg, tinfo = M.config(), M.config(fusion=M.MRW_FUSE_NONE), {"note": "default configuration"}
+        tf = timed(launcher(ftree, sets, f_cfg), reps)
+        # the bytes that were timed: sampled rows of every output set against the oracle's stages
+        # on the same rows (global row offsets for the noise hash)
+        rows = np.unique(np.linspace(0, side - 1, 24).astype(np.int64))
+        want = np.stack([O.mirror(O.solarise(O.noise(img[r:r + 1], seed, 0, int(r))))[0] for r in rows])
+        ridx = torch.from_numpy(rows).to(ctx["device"])
+
+        def bad_sets():
+            return [k for k, y in enumerate(outs) if not np.array_equal(y.index_select(0, ridx).cpu().numpy(), want)]
+        bad_fused = bad_sets()
+        tu = timed(launcher(ftree, sets, u_cfg), reps)
+        bad_unfused = bad_sets()
+        checked = not bad_fused and not bad_unfused
+        b = 2 * side * side
+        rec = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2), "tuned": tinfo,
+               "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
+               "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+               "roofline": alu_roofline(side * side / tf, pipes, ctx["sm_mhz"]),
+               "l2": (f"resident ({b >> 20} MiB)" if nsets == 1 and side <= 2048 else
+                      f"{nsets} rotating sets, {nsets * b >> 20} MiB"),
+               "checked": bool(checked), "check": f"{len(rows)} rows of each of the {nsets} outputs, byte for byte"
+                                                  + ("" if checked else f"; differing sets: fused {bad_fused}, "
+                                                                        f"per stage {bad_unfused}")}
+        rec["roofline"]["frac_hbm"] = rec["frac_hbm"]
+        if ctx["cpu"]:
+            nr = max(1, min(side, (4 << 20) // side))  # a bounded sample: about 4 MiB of rows
+            blocks = [(r0, min(nr, r0 + max(1, nr // host_cores()))) for r0 in range(0, nr, max(1, nr // host_cores()))]
+            jobs = [lambda a=a, e=e: O.mirror(O.solarise(O.noise(img[a:e], seed, 0, a))) for a, e in blocks]
+            rec["cpu_baseline"] = oracle_rate(jobs, 2 * nr * side / 1e9, "GB/s",
+                                              f"oracle noise/solarise/mirror on the first {nr} rows "
+                                              f"({nr * side >> 10} KiB) in {len(jobs)} row blocks")
+        out[f"filter_{side}"] = rec
+    return out
+
+
+def fft_workload(ctx, nfft=256):
     """FFT pipelined with its inversion (Section 4): 256 rows of 65536 complex float32 values
     (one 512 KB elementary unit each, 128 MB in total); forward then inverse transform of every
     row, fused on chip (one cluster launch) and kernel per stage (two launches through HBM)."""
     import torch
 
+    from oracle import fft as OF
     from paper_1510_06585_gb300 import inputs
+    M, timed, launcher, peaks = ctx["M"], ctx["timed"], ctx["launcher"], ctx["peaks"]
     n = 65536
-    x = torch.from_numpy(inputs.fft_signals(nfft, n)).to(device)
+    sig = inputs.fft_signals(nfft, n)
+    x = torch.from_numpy(sig).to(ctx["device"])
     y = torch.empty_like(x)
     tree = M.pipeline(M.stage("fft"), M.stage("ifft"))
     sets = [M.buffers(x, y)]
+    fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
     tf = timed(launcher(tree, sets, fused), 20)
+    want = OF.pipeline(sig, ["fft", "ifft"])
+    err_f = OF.rel_error(y.cpu().numpy(), want)
     tu = timed(launcher(tree, sets, unfused), 20)
+    err_u = OF.rel_error(y.cpu().numpy(), want)
     b = 2 * nfft * n * 8                      # read the input once, write the output once
     flop = 2 * 5.0 * n * 16 * nfft            # 5 N log2 N per transform, two transforms
-    return {f"fft_ifft_{nfft}x65536": {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 1),
-                                       "gflops": round(flop / tf / 1e9, 1),
-                                       "kernel_per_stage_gbs": round(b / tu / 1e9, 1),
-                                       "speedup_fused": round(tu / tf, 3),
-                                       "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
-                                       "bytes": b, "l2": "128 MB in + 128 MB out per step (> L2)"}}
+    rec = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 1), "gflops": round(flop / tf / 1e9, 1),
+           "kernel_per_stage_gbs": round(b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
+           "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4), "bytes": b,
+           "roofline": {"bound": "hbm", "frac": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+                        "achieved": round(b / tf / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s"},
+           "l2": "128 MB in + 128 MB out per step (> L2)",
+           "checked": bool(err_f <= 1e-5 and err_u <= 1e-5),
+           "check": f"all {nfft} rows against the oracle's fft then ifft, normwise error per row "
+                    f"{err_f:.2e} fused, {err_u:.2e} per stage (bound 1e-5)"}
+    if ctx["cpu"]:
+        rows = 4
+        jobs = [lambda k=k: OF.pipeline(sig[k:k + rows], ["fft", "ifft"]) for k in range(0, 64, rows)]
+        rec["cpu_baseline"] = oracle_rate(jobs, 64 * n * 16 / 1e9, "GB/s",
+                                          f"oracle fft then ifft of 64 of the {nfft} rows (4 rows per call)")
+    return {f"fft_ifft_{nfft}x65536": rec}
+
+
+def saxpy_workload(ctx, sizes=(10 ** 6, 10 ** 7, 10 ** 8), stages=4):
+    """Saxpy Map (Section 4, Saxpy): y = a x + y on float32 vectors of 10^6 .. 10^8 elements,
+    12 algorithmic bytes per element and stage pass (read x and y, write y); and a Map of `stages`
+    saxpy stages at the largest size, fused into one pass against one pass per stage."""
+    import torch
+
+    from oracle import saxpy as OS
+    M, timed, launcher, peaks = ctx["M"], ctx["timed"], ctx["launcher"], ctx["peaks"]
+    out = {}
+    alphas = [2.0, -0.5, 0.25, 1.5][:stages]
+    for n in sizes:
+        rng = np.random.Generator(np.random.PCG64(8))
+        x0 = rng.uniform(-1, 1, size=n).astype(np.float32)
+        y0 = rng.uniform(-1, 1, size=n).astype(np.float32)
+        nsets = max(1, -(-(512 << 20) // (12 * n)))  # rotating sets: at least 512 MiB between reuses
+        xs = [torch.from_numpy(x0).to(ctx["device"]) for _ in range(nsets)]
+        ys = [torch.from_numpy(y0).to(ctx["device"]) for _ in range(nsets)]
+        sets = [M.buffers(x, y) for x, y in zip(xs, ys)]
+        trees = [(1, M.map_(M.stage("saxpy", alpha=alphas[0])))]
+        if n == max(sizes):
+            trees.append((stages, M.map_(M.pipeline(*[M.stage("saxpy", alpha=a) for a in alphas]))))
+        for k, tree in trees:
+            reps = 200 if n <= 10 ** 6 else 20
+            tf = timed(launcher(tree, sets, M.config()), reps)
+            tu = timed(launcher(tree, sets, M.config(fusion=M.MRW_FUSE_NONE)), reps)
+            # the bits that were timed: one more run of the fused plan from the initial vectors
+            ys[0].copy_(torch.from_numpy(y0))
+            launcher(tree, sets[:1], M.config())(0)
+            torch.cuda.synchronize()
+            ctx["drain"]()
+            got = ys[0].cpu().numpy()
+            idx = np.arange(0, n, 7)
+            err = np.abs(got[idx].astype(np.float64) - OS.saxpy_stages(x0[idx], y0[idx], alphas[:k]))
+            ok = bool((err <= OS.error_bound(x0[idx], y0[idx], alphas[:k])).all())
+            b = 12 * n
+            rec = {"fused_gbs": round(b / tf / 1e9, 1), "fused_us": round(tf * 1e6, 2), "stages": k,
+                   "kernel_per_stage_gbs": round(k * b / tu / 1e9, 1), "speedup_fused": round(tu / tf, 3),
+                   "frac_hbm": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+                   "roofline": {"bound": "hbm", "frac": round(b / tf / 1e9 / peaks["hbm_gbs"], 4),
+                                "achieved": round(b / tf / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                "bytes_per_element": 12},
+                   "l2": f"{nsets} rotating sets, {nsets * b >> 20} MiB" if nsets > 1 else f"{b >> 20} MiB per set",
+                   "checked": ok, "check": f"every 7th element within the FP64 oracle's rounding bound of "
+                                           f"{k} float32 multiply-add(s)",
+                   "note": "kernel_per_stage_gbs counts the bytes of every pass"}
+            if ctx["cpu"]:
+                m = min(n, 4 * 10 ** 6)
+                cut = np.linspace(0, m, host_cores() + 1).astype(np.int64)
+                jobs = [lambda a=a, e=e: OS.saxpy_stages(x0[a:e], y0[a:e], alphas[:k]) for a, e in zip(cut, cut[1:])
+                        if e > a]
+                rec["cpu_baseline"] = oracle_rate(jobs, 12 * m / 1e9, "GB/s",
+                                                  f"oracle saxpy ({k} stage(s)) on the first {m} elements in "
+                                                  f"{len(jobs)} blocks; GB/s at 12 bytes per element")
+            out[f"saxpy_{n}" + (f"_x{k}" if k > 1 else "")] = rec
+    return out
 
 
 def costmodel_workload(n_train=4000, n_test=500, max_log2=26):
@@ -514,41 +754,79 @@ def costmodel_workload(n_train=4000, n_test=500, max_log2=26):
                           "train_seconds": res["train_seconds"], "seconds": round(time.perf_counter() - t0, 1)}}
 
 
-def nbody_workload(M, device, timed, launcher, fused, unfused):
+def nbody_workload(ctx):
     import torch
 
+    from oracle import nbody as ON
     from paper_1510_06585_gb300 import inputs
+    M, timed, launcher = ctx["M"], ctx["timed"], ctx["launcher"]
     out = {}
     # N-body: accel + Loop(100 KDK)
-    n = 65536
+    n, steps = 65536, 100
     xs, vs, as_ = inputs.nbody(n)
-    st = [torch.from_numpy(t).to(device) for t in (xs, vs, as_)]
+    st = [torch.from_numpy(t).to(ctx["device"]) for t in (xs, vs, as_)]
     kdk = M.stage("nbody_kdk", eps=1e-3, dt=1e-3)
-    ntree = M.pipeline(M.stage("nbody_accel", eps=1e-3, dt=1e-3), M.loop(kdk, 100))
+    ntree = M.pipeline(M.stage("nbody_accel", eps=1e-3, dt=1e-3), M.loop(kdk, steps))
     nb = [M.buffers(*st)]
+    fused, unfused = M.config(), M.config(fusion=M.MRW_FUSE_NONE)
     tn = timed(launcher(ntree, nb, fused), 3, warm=1)
     tnu = timed(launcher(ntree, nb, unfused), 1, warm=0)
-    inter = float(n) * n * 101
+    # the trajectory that was timed, from the initial state once more, against the FP64 oracle's
+    # end state of every body (tests/golden, written by a script that calls only the oracle)
+    for t, a in zip(st, (xs, vs, as_)):
+        t.copy_(torch.from_numpy(a))
+    launcher(ntree, nb, fused)(0)
+    torch.cuda.synchronize()
+    ctx["drain"]()
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "nbody_65536_100steps.npz"))
+    xg, vg = st[0].cpu().numpy(), st[1].cpu().numpy()
+    pos_err = ON.pos_rel_error(xg, gold["x"])
+    vel_err = ON.vel_rel_error(vg, gold["v"])
+    p = ON.momentum(xg, vg)
+    mom = float(np.linalg.norm(p) / (xg[:, 3:4].astype(np.float64) * np.abs(vg[:, :3])).sum())
+    inter = float(n) * n * (steps + 1)
     alu_peak = 20.0 * 152 * 128 * 2070e6 / 12 / 1e9  # GFLOP/s at 12 FP32-pipe instructions per interaction
     gf = 20.0 * inter / tn / 1e9
-    out["nbody_65536x100"] = {"gflops": round(gf, 1), "ms": round(tn * 1e3, 2),
-                              "interactions_per_s": round(inter / tn, 1),
-                              "frac_alu": round(gf / alu_peak, 4), "alu_peak_gflops": round(alu_peak, 1),
-                              "kernel_per_step_host_loop_ms": round(tnu * 1e3, 2),
-                              "speedup_fused": round(tnu / tn, 3)}
+    rec = {"gflops": round(gf, 1), "ms": round(tn * 1e3, 2), "interactions_per_s": round(inter / tn, 1),
+           "frac_alu": round(gf / alu_peak, 4), "alu_peak_gflops": round(alu_peak, 1),
+           "roofline": {"bound": "alu", "frac": round(gf / alu_peak, 4), "achieved": round(gf, 1),
+                        "peak": round(alu_peak, 1), "unit": "GFLOP/s",
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 FP32-pipe instructions "
+                                       "per interaction, 20 flop each"},
+           "kernel_per_step_host_loop_ms": round(tnu * 1e3, 2), "speedup_fused": round(tnu / tn, 3),
+           "checked": bool(pos_err <= 1e-4 and vel_err <= 1e-3 and mom <= 1e-4),
+           "check": f"all {n} bodies after {steps} steps against the FP64 oracle: position error {pos_err:.2e} "
+                    f"(bound 1e-4), velocity error {vel_err:.2e} of max |v| (bound 1e-3), momentum {mom:.1e}"}
+    if ctx["cpu"]:
+        g = ON.gravity(n)
+        a0 = ON.accel(xs, g)  # a(x0), outside the timing (it is the loop's entry state)
+        t0 = time.perf_counter()
+        ON.kdk(xs, np.zeros((n, 3)), a0, 1, g, threads=host_cores())
+        dt = time.perf_counter() - t0
+        rec["cpu_baseline"] = {"value": round(20.0 * n * n / dt / 1e9, 2), "unit": "GFLOP/s", "cores": host_cores(),
+                               "kind": "oracle",
+                               "sample": f"one FP64 kick-drift-kick step of all {n} bodies (one force evaluation, "
+                                         f"{n * n:.3g} interactions) in C on {host_cores()} threads; the 100-step "
+                                         f"run extrapolates to {dt * (steps + 1):.0f} s (101 evaluations)",
+                               "seconds": round(dt, 2), "extrapolated_run_s": round(dt * (steps + 1), 1)}
+    out["nbody_65536x100"] = rec
     return out
 
 
-def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stream, batch_n):
+def batched_workload(ctx, batch_n):
     import torch
 
+    from oracle import batch as OB
+    from oracle import image as O
     from paper_1510_06585_gb300 import inputs
+    M, lib, timed, pending, peaks, stream = (ctx["M"], ctx["lib"], ctx["timed"], ctx["pending"], ctx["peaks"],
+                                             ctx["stream"])
     out = {}
     # Batched: instances of Filter Pipeline + 5x5 blur, sides log-uniform in 64..2048
     shapes = inputs.batch_shapes(batch_n)
     desc, nbytes = inputs.batch_descriptors(shapes)
     arena = inputs.batch_arena(desc, nbytes)
-    bx = torch.from_numpy(arena).to(device)
+    bx = torch.from_numpy(arena).to(ctx["device"])
     by = torch.zeros_like(bx)
     btree = M.map_(M.pipeline(M.stage("noise"), M.stage("solarise"), M.stage("mirror"), M.stage("blur5")))
     d = np.ascontiguousarray(desc, dtype=np.int64)
@@ -565,39 +843,65 @@ def batched_workload(M, lib, device, timed, pending, fused, unfused, peaks, stre
     px = float((shapes[:, 0] * shapes[:, 1]).sum())
     # autotune the batched launch over the candidate tile shapes (fused and kernel-per-stage)
     cand = M.tune_candidates(btree, [bx[:64].view(8, 8), by[:64].view(8, 8)])
-    times = [timed(blaunch(c), 2, warm=1) for c in cand]
-    bf = min(range(8), key=lambda i: times[i])
-    bu = min(range(8, 16), key=lambda i: times[i])
+    if ctx["tune"]:
+        times = [timed(blaunch(c), 2, warm=1) for c in cand]
+        bf = min(range(8), key=lambda i: times[i])
+        bu = min(range(8, 16), key=lambda i: times[i])
+    else:
+        times, bf, bu = [float("nan")] * 16, 0, 8
     tb = timed(blaunch(cand[bf]), 5)
+    # the bytes that were timed: oracle digests of a sample of instances (the smallest, the largest
+    # and every 64th) against the same instances of the output
+    area = shapes[:, 0] * shapes[:, 1]
+    sample = sorted(set([int(np.argmin(area)), int(np.argmax(area))] + list(range(0, batch_n, 64))))
+    want = {i: OB.instance_digest((i, desc[i, 1], desc[i, 2], desc[i, 4]))[1] for i in sample}
+
+    def ok_instances():
+        res = by.cpu().numpy()
+        return all(OB.digest(inputs.instance_view(res, desc[i])) == want[i] for i in sample)
+    checked = ok_instances()
+    by.zero_()
     tbu = timed(blaunch(cand[bu]), 3)
+    checked = checked and ok_instances()
     # where the time goes: the same batch and launch shape with the leading stages removed
     subsets = {}
     for names in (["blur5"], ["mirror", "blur5"], ["solarise", "mirror", "blur5"]):
         sub = M.map_(M.pipeline(*[M.stage(nm) for nm in names]))
         subsets["+".join(names)] = round(timed(blaunch(cand[bf], sub), 3) * 1e3, 3)
-    out[f"batched_{batch_n}"] = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
-                           "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
-                           "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
-                           "launches_per_step": 1, "stage_subsets_ms": subsets,
-                           "tuned": {"fused_index": bf, "fused_cfg": list(cand[bf].as_tuple()),
-                                                             "unfused_index": bu,
-                                                             "default_ms": round(times[0] * 1e3, 4)}}
+    pipes = recorded_pipes("k_stencil.cu", "batched_stencil_rows")
+    rec = {"fused_gbs": round(2 * px / tb / 1e9, 1), "fused_ms": round(tb * 1e3, 3),
+           "pixels": int(px), "kernel_per_stage_gbs": round(2 * px / tbu / 1e9, 1),
+           "speedup_fused": round(tbu / tb, 3), "frac_hbm": round(2 * px / tb / 1e9 / peaks["hbm_gbs"], 4),
+           "roofline": alu_roofline(px / tb, pipes, ctx["sm_mhz"]),
+           "launches_per_step": 1, "stage_subsets_ms": subsets,
+           "tuned": {"fused_index": bf, "fused_cfg": list(cand[bf].as_tuple()), "unfused_index": bu,
+                     "default_ms": round(times[0] * 1e3, 4)},
+           "checked": bool(checked),
+           "check": f"oracle BLAKE2b digests of {len(sample)} instances (smallest, largest, every 64th) after the "
+                    f"fused and the kernel-per-stage runs"}
+    rec["roofline"]["frac_hbm"] = rec["frac_hbm"]
+    if ctx["cpu"]:
+        take = list(range(0, batch_n, max(1, batch_n // 192)))[:192]
+        views = [(inputs.instance_view(arena, desc[i]).copy(), int(desc[i, 4])) for i in take]
+        jobs = [lambda v=v, sd=sd: O.filter_blur_pipeline(v, sd) for v, sd in views]
+        spx = float(sum(v.size for v, _ in views))
+        rec["cpu_baseline"] = oracle_rate(jobs, 2 * spx / 1e9, "GB/s",
+                                          f"oracle Filter Pipeline + blur of {len(views)} of the {batch_n} instances "
+                                          f"({int(spx)} pixels)")
+    out[f"batched_{batch_n}"] = rec
     return out
 
 
 def cpu_baseline(vol, min_seconds=8.0):
-    """The oracle as it stands on a bounded sample of the workload (the first 128 planes)."""
+    """The oracle as it stands on the host's cores, on a bounded sample of the workload (the
+    first 128 planes, in blocks of 4 planes on as many threads as the host has cores)."""
     from oracle import image as O
     sample = vol[:128]
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < min_seconds:
-        O.segmentation(sample)
-        reps += 1
-    dt = time.perf_counter() - t0
-    b = (2 * sample.size + 24) * reps
-    return {"value": round(b / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x Map+MapReduce on the first 128 of 512 planes (32 MiB), numpy single thread",
-            "seconds": round(dt, 2)}
+    jobs = [lambda k=k: O.segmentation(sample[k:k + 4]) for k in range(0, 128, 4)]
+    rec = oracle_rate(jobs, (2 * sample.size + 24) / 1e9, "GB/s",
+                      "Map+MapReduce on the first 128 of 512 planes (32 MiB) in 32 blocks of 4 planes",
+                      min_seconds=min_seconds)
+    return rec
 
 
 def run_reference(args):
@@ -605,15 +909,20 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from concurrent.futures import ThreadPoolExecutor
+
     from oracle import image as O
     from paper_1510_06585_gb300 import inputs
-    sample = inputs.volume(32, 512, 512)  # a bounded sample of the workload per step (8 MiB)
-    for _ in range(args.warmup):
-        O.segmentation(sample)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.segmentation(sample)
-    dt = time.perf_counter() - t0
+    sample = inputs.volume(64, 512, 512)  # a bounded sample of the workload per step (16 MiB)
+    cores = host_cores()
+    jobs = [lambda k=k: O.segmentation(sample[k:k + 4]) for k in range(0, 64, 4)]
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for _ in range(args.warmup):
+            list(ex.map(lambda f: f(), jobs))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            list(ex.map(lambda f: f(), jobs))
+        dt = time.perf_counter() - t0
     b = (2 * sample.size + 24) * args.steps
     v = b / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
@@ -621,9 +930,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded 3-component mixture volume)",
             "config": {"workload": WORKLOAD, "shape": list(SEG_SHAPE)},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: Map+MapReduce on 32 of the 512 planes (8 MiB in, 8 MiB of "
-                                       "labels out), numpy single thread; GB/s = bytes of the sample / time"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": min(cores, len(jobs)), "kind": "oracle",
+                             "sample": "each step: Map+MapReduce on 64 of the 512 planes (16 MiB in, 16 MiB of "
+                                       "labels out) in 16 blocks of 4 planes on the host's cores; GB/s = bytes of "
+                                       "the sample / time"},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -635,8 +945,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrw", choices=["mrw", "reference"])
     ap.add_argument("--no-extras", dest="extras", action="store_false")
-    ap.add_argument("--workloads", default="filter,nbody,batched,fft,costmodel",
-                    help="comma list of the extra workloads to run (filter, nbody, batched, fft, costmodel)")
+    ap.add_argument("--workloads", default="filter,nbody,batched,fft,saxpy,costmodel",
+                    help="comma list of the extra workloads to run (filter, nbody, batched, fft, saxpy, costmodel)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="extra workloads run their default configuration (profiling runs: no tuner launches)")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false",
+                    help="skip timing the oracle on the host's cores")
+    ap.add_argument("--no-coexec", dest="coexec", action="store_false",
+                    help="skip the CPU + GPU co-executed segmentation")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--filter-sides", default="1024,4096,8192,16384", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--fused-cfg", default="",
