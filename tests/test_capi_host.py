@@ -290,3 +290,15 @@ def test_saxpy_stages_fuse_into_passes_of_64(lib):
     assert d["family"] == "saxpy" and d["stages"] == 100 and d["launches"] == 2 and d["n"] == 1000
     assert mrw.plan_describe(tree, [x, y], mrw.config(fusion=mrw.MRW_FUSE_NONE))["launches"] == 100
     assert mrw.plan_describe(tree, [x, y], mrw.config(unroll=8))["grid"] == 1
+
+
+def test_batched_descriptor_offsets_near_int64_max_are_rejected_before_any_launch(lib):
+    # validation runs before anything touches the GPU or the arenas (the pointers are never used)
+    tree = mrw.map_(mrw.pipeline(mrw.stage("noise"), mrw.stage("blur5")))
+    desc = np.array([[0, 8, 8, 16, 1], [(1 << 63) - 16, 8, 8, 16, 2]], dtype=np.int64)
+    dptr = desc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    fut = ctypes.c_void_p()
+    a, b = 1 << 20, 1 << 21  # two non-overlapping 16-byte aligned addresses, 4096 bytes each
+    assert lib.mrw_execute_batched(tree.h, a, b, 4096, dptr, 2, None, None, ctypes.byref(fut)) == mrw.MRW_ERR_SHAPE
+    assert lib.mrw_execute_batched_noalloc(tree.h, a, b, 4096, dptr, 2, None, None) == mrw.MRW_ERR_SHAPE
+    assert b"outside the arena" in lib.mrw_last_error()
