@@ -83,7 +83,8 @@ typedef struct mrw_buffer {
   mrw_dtype dtype;
   int32_t ndim;                 /* 1..4                                                      */
   int64_t shape[MRW_MAX_DIMS];  /* outermost first; an image is (H, W), a volume (D, H, W),
-                                   an N-body state array (N, 4)                              */
+                                   an N-body state array (N, 4); every extent >= 1 (an empty
+                                   buffer is refused with MRW_ERR_SHAPE before any launch)    */
   int64_t pitch;                /* bytes between consecutive rows (innermost dimension);
                                    0 = dense. Device image buffers need pitch % 16 == 0 and a
                                    16-byte-aligned `data`, and must span rows * pitch bytes  */

@@ -302,3 +302,29 @@ def test_batched_descriptor_offsets_near_int64_max_are_rejected_before_any_launc
     assert lib.mrw_execute_batched(tree.h, a, b, 4096, dptr, 2, None, None, ctypes.byref(fut)) == mrw.MRW_ERR_SHAPE
     assert lib.mrw_execute_batched_noalloc(tree.h, a, b, 4096, dptr, 2, None, None) == mrw.MRW_ERR_SHAPE
     assert b"outside the arena" in lib.mrw_last_error()
+
+
+def test_empty_buffers_are_refused_before_any_launch(lib):
+    fut = ctypes.c_void_p()
+    cases = [
+        (mrw.pipeline(mrw.stage("noise", seed=1)), [np.zeros((0, 16), np.uint8), np.zeros((0, 16), np.uint8)]),
+        (mrw.mapreduce(mrw.map_(mrw.stage("threshold3"))),
+         [np.zeros((4, 0, 16), np.uint8), np.zeros((4, 0, 16), np.uint8), np.zeros(3, np.int64)]),
+        (mrw.map_(mrw.stage("saxpy", alpha=2.0)), [np.zeros(0, np.float32), np.zeros(0, np.float32)]),
+        (mrw.stage("nbody_accel", eps=1e-3), [np.zeros((0, 4), np.float32)] * 3),
+        (mrw.pipeline(mrw.stage("fft")), [np.zeros((0, 65536), np.complex64)] * 2),
+    ]
+    keep = []
+    for tree, args in cases:
+        arr = (mrw.mrw_buffer * len(args))()
+        for i, a in enumerate(args):  # described by hand: numpy gives empty arrays arbitrary strides
+            b = np.zeros(16, np.uint8)
+            keep.append(b)
+            arr[i].data = b.ctypes.data
+            arr[i].dtype = mrw._dtype_code(a.dtype)
+            arr[i].ndim = a.ndim
+            for d, e in enumerate(a.shape):
+                arr[i].shape[d] = e
+            arr[i].memory = mrw.MRW_MEM_HOST
+        assert lib.mrw_execute(tree.h, arr, len(args), None, None, ctypes.byref(fut)) == mrw.MRW_ERR_SHAPE
+        assert not fut.value
