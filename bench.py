@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fused skeleton GB/s & % HBM peak vs kernel-per-stage; N-body GFLOP/s"
 SEG_SHAPE = (512, 512, 512)
-SEG_BYTES = 2 * 512 ** 3 + 24
+SEG_N = 512 ** 3
+SEG_BYTES = 2 * SEG_N + 24
 WORKLOAD = "segmentation 512^3 u8: Map(threshold 85/170 -> labels) + MapReduce(+) int64 class counts"
 
 
@@ -392,7 +393,7 @@ def run_mrw(args):
         cur.wait_stream(s_out)
     k_link = max(1, min(K, 20))
     t_link = time_steps(link_step, k_link, min(W, 3), world, device)
-    link_gbs = world * 2 * 512 ** 3 * k_link / t_link / 1e9
+    link_gbs = world * 2 * SEG_N * k_link / t_link / 1e9
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -406,14 +407,15 @@ def run_mrw(args):
                              "speedup_fused": round(unfused_s / fused_s, 3)},
         "roofline": {"bound": "hbm", "achieved": round(SEG_BYTES / fused_s / 1e9, 2), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(SEG_BYTES / fused_s / 1e9 / peaks["hbm_gbs"], 4),
-                     "traffic": recorded_traffic("k_chain.cu", "segmentation_512cubed_chain"),
+                     "traffic": (recorded_traffic("k_chain.cu", "segmentation_512cubed_chain")
+                                 if SEG_SHAPE[0] == 512 else None),
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
-                     "copy_same_size_gbs": round(2 * 512 ** 3 / t_copy / 1e9, 2),
-                     "frac_of_copy_same_size": round((2 * 512 ** 3 / fused_s) / (2 * 512 ** 3 / t_copy), 4),
+                     "copy_same_size_gbs": round(2 * SEG_N / t_copy / 1e9, 2),
+                     "frac_of_copy_same_size": round(t_copy / fused_s, 4),
                      "note": "achieved = algorithmic bytes / CUDA-event time of the step (the chain kernel and the "
                              "one-CTA MapReduce finish kernel behind it)"},
-        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 512 ** 3,
-                "d2h_bytes_per_step": 512 ** 3 + 24, "steps": k_e2e,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": SEG_N,
+                "d2h_bytes_per_step": SEG_N + 24, "steps": k_e2e,
                 "host_link_copy_gbs": round(link_gbs, 2), "frac_of_host_link": round(e2e_value / link_gbs, 4),
                 "cfg": list(e2e_cfg.as_tuple()), "checked": e2e_checked,
                 "note": "pinned host buffers read and written in place over NVLink-C2C by the fused kernel; "
@@ -953,6 +955,8 @@ def main():
                     help="skip timing the oracle on the host's cores")
     ap.add_argument("--no-coexec", dest="coexec", action="store_false",
                     help="skip the CPU + GPU co-executed segmentation")
+    ap.add_argument("--seg-depth", type=int, default=512,
+                    help="planes of the segmentation volume (profiling runs of a smaller case; the headline is 512)")
     ap.add_argument("--batch-n", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--filter-sides", default="1024,4096,8192,16384", help="image sides of the Filter Pipeline workload")
     ap.add_argument("--fused-cfg", default="",
@@ -961,6 +965,12 @@ def main():
     ap.add_argument("--no-segmentation", dest="segmentation", action="store_false",
                     help="skip the headline timing (profiling runs of one extra workload)")
     args = ap.parse_args()
+    global SEG_SHAPE, SEG_N, SEG_BYTES, WORKLOAD
+    if args.seg_depth != 512:
+        SEG_SHAPE = (args.seg_depth, 512, 512)
+        SEG_N = args.seg_depth * 512 * 512
+        SEG_BYTES = 2 * SEG_N + 24
+        WORKLOAD = WORKLOAD.replace("512^3", f"{args.seg_depth}x512x512")
     if args.warmup < 3 and args.impl == "mrw":
         args.warmup = 3
     if args.impl == "reference":

@@ -77,3 +77,38 @@ def test_sum_reduction_into_a_device_result_and_rejections():
     with pytest.raises(M.MrwError) as e:
         M.Balancer().execute(M.pipeline(M.stage("solarise"), M.stage("blur5")), [vol, out])
     assert e.value.status == M.MRW_ERR_UNSUPPORTED
+
+
+def test_random_trees_and_splits_match_the_oracle():
+    # random pointwise chains (noise seeds, mirrors, solarise, thresholds), with or without a
+    # MapReduce root, on images and volumes of odd widths, at random GPU shares: the host workers'
+    # rows and the GPU's rows together must be the oracle's output, whatever the split
+    rng = np.random.Generator(np.random.PCG64(31))
+    kinds = ["noise", "solarise", "mirror", "threshold3"]
+    for case in range(12):
+        n = int(rng.integers(1, 6))
+        names = [kinds[int(k)] for k in rng.integers(0, 4, size=n)]
+        while names.count("noise") > 2:  # at most two noise stages fuse into one kernel
+            names.remove("noise")
+        seeds = {i: int(rng.integers(0, 2 ** 31)) for i, nm in enumerate(names) if nm == "noise"}
+        h, w = int(rng.integers(1, 90)), int(rng.integers(1, 300))
+        img = (inputs.volume(int(rng.integers(1, 4)), h, w, seed=case) if case % 2 else
+               inputs.filter_image(h, w, seed=case))
+        body = M.pipeline(*[M.stage(nm, seed=seeds.get(i, 0)) if nm == "noise" else M.stage(nm)
+                            for i, nm in enumerate(names)])
+        oracle = ("pipeline", [("stage", nm, {"seed": seeds.get(i, 0)}) for i, nm in enumerate(names)])
+        reduce = bool(case % 3 == 0)
+        share = float(rng.uniform(0, 1))
+        out = np.zeros_like(img)
+        if reduce:
+            tree = M.mapreduce(M.map_(body))
+            want, total = S.evaluate_image(("mapreduce", ("map", oracle), "add"), img)
+            k = 3 if names[-1] == "threshold3" else 1
+            res = np.full(k, -1, np.int64)
+            M.Balancer(gpu_share=share).execute(tree, [img, out, res])
+            assert np.array_equal(res, total), (case, names, share)
+        else:
+            tree = M.map_(body)
+            want, _ = S.evaluate_image(("map", oracle), img)
+            M.Balancer(gpu_share=share).execute(tree, [img, out])
+        assert np.array_equal(out, want), (case, names, share, img.shape)
