@@ -1,5 +1,6 @@
 """GPU parity of the TMA-staged stencil groups (5x5 box blur fused with pointwise prefixes and
 suffixes) and of batched execution, against the CPU oracle: bit-exact."""
+import ctypes
 import os
 
 import numpy as np
@@ -197,3 +198,55 @@ def test_while_loop_inside_a_pipeline_and_capped_bodies():
     # an idempotent pointwise body stops after its second run
     got, _ = run_image(M.loop(M.stage("solarise"), 50, M.MRW_LOOP_WHILE_CHANGED), img)
     assert np.array_equal(got, O.solarise(img))
+
+
+def test_batched_plan_cache_eviction_under_concurrent_callers():
+    # Four host threads, each on its own stream, run batched launches with 48 distinct descriptor
+    # tables between them (more than the 32 cached plans): entries are evicted while other
+    # threads hold and launch theirs. Every output must still be the oracle's.
+    import threading
+
+    from oracle import batch as OB
+    lib = M.load()
+    tree = M.map_(M.pipeline(M.stage("noise"), M.stage("solarise"), M.stage("mirror"), M.stage("blur5")))
+    jobs = []
+    for k in range(48):
+        rng = np.random.Generator(np.random.PCG64(900 + k))
+        shapes = np.stack([rng.integers(1, 70, size=3), rng.integers(1, 50, size=3)], axis=1)
+        desc, nbytes = inputs.batch_descriptors(shapes)
+        arena = inputs.batch_arena(desc, nbytes, seed=900 + k)
+        want = [OB.digest(O.filter_blur_pipeline(inputs.instance_view(arena, d), int(d[4]))) for d in desc]
+        jobs.append((np.ascontiguousarray(desc, dtype=np.int64), arena, want))
+    errors = []
+
+    def worker(tid):
+        try:
+            stream = torch.cuda.Stream()
+            for rep in range(2):
+                for k in range(tid, 48, 4):
+                    desc, arena, want = jobs[k]
+                    x = torch.from_numpy(arena).cuda()
+                    y = torch.zeros_like(x)
+                    torch.cuda.synchronize()
+                    fut = ctypes.c_void_p()
+                    st = lib.mrw_execute_batched(tree.h, x.data_ptr(), y.data_ptr(), x.numel(),
+                                                 desc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                 desc.shape[0], None, stream.cuda_stream, ctypes.byref(fut))
+                    if st != M.MRW_OK:
+                        errors.append((tid, k, "status", st))
+                        continue
+                    st = lib.mrw_future_wait(fut, 120000)
+                    lib.mrw_future_release(fut)
+                    out = y.cpu().numpy()
+                    got = [OB.digest(inputs.instance_view(out, d)) for d in desc]
+                    if st != M.MRW_OK or got != want:
+                        errors.append((tid, k, rep, st))
+        except Exception as e:  # reported below
+            errors.append((tid, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors[:5]
