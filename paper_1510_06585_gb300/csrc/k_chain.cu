@@ -458,6 +458,16 @@ cudaError_t launch_chain_finish(unsigned long long *partials, unsigned long long
   return cudaLaunchKernelEx(&cfg, chain_finish_kernel, partials, red, nout);
 }
 
+cudaError_t chain_node(const ChainArgs &ca, int n_noise, int unroll, int grid, int block, NodeChain &nc) {
+  if (grid <= 0) return cudaSuccess;
+  ChainArgs a = ca;  // copied into the node's parameters by cudaGraphAddKernelNode
+  a.pattern = op_pattern(a.ops, a.nops, &a.pattern_t);
+  const void *fn = pick(n_noise, a.mirror != 0, unroll);
+  if (!fn) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&a};
+  return nc.kernel(fn, dim3(grid), dim3(block), 0, args);
+}
+
 cudaError_t launch_chain(const ChainArgs &ca, int n_noise, int unroll, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
   ChainArgs a = ca;

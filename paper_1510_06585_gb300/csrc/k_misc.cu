@@ -52,11 +52,6 @@ __global__ void __launch_bounds__(256) saxpy_kernel(const __grid_constant__ Saxp
   }
 }
 
-__global__ void fill_u32_kernel(unsigned int *p, unsigned int v, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = v;
-}
-
 // a := b where they differ (rows of W bytes, both with `pitch`, 16-byte aligned rows) and
 // *changed := 1 if any byte differed.
 __global__ void compare_copy_kernel(const uint8_t *__restrict__ b, uint8_t *__restrict__ a, int64_t rows, int32_t W,
@@ -107,22 +102,22 @@ __global__ void while_init_kernel(LoopCtrl *ctrl, unsigned int *words, unsigned 
 
 }  // namespace
 
-cudaError_t launch_compare_copy(const uint8_t *b, uint8_t *a, int64_t rows, int32_t W, int64_t pitch,
-                                unsigned int *changed, int sms, cudaStream_t s) {
+cudaError_t compare_copy_node(const uint8_t *b, uint8_t *a, int64_t rows, int32_t W, int64_t pitch,
+                              unsigned int *changed, int sms, NodeChain &nc) {
   const int64_t n = rows * ((W + 15) / 16);
   const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-  compare_copy_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(b, a, rows, W, pitch, changed);
-  return cudaGetLastError();
+  void *args[] = {(void *)&b, (void *)&a, (void *)&rows, (void *)&W, (void *)&pitch, (void *)&changed};
+  return nc.kernel((const void *)compare_copy_kernel, dim3(grid > 0 ? grid : 1), dim3(256), 0, args);
 }
 
-cudaError_t launch_while_control(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, cudaStream_t s) {
-  while_control_kernel<<<1, 1, 0, s>>>(ctrl, changed, h);
-  return cudaGetLastError();
+cudaError_t while_control_node(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, NodeChain &nc) {
+  void *args[] = {(void *)&ctrl, (void *)&changed, (void *)&h};
+  return nc.kernel((const void *)while_control_kernel, dim3(1), dim3(1), 0, args);
 }
 
-cudaError_t launch_while_init(LoopCtrl *ctrl, unsigned int *changed, unsigned long long max_iters, cudaStream_t s) {
-  while_init_kernel<<<1, 1, 0, s>>>(ctrl, changed, max_iters);
-  return cudaGetLastError();
+cudaError_t while_init_node(LoopCtrl *ctrl, unsigned int *words, unsigned long long max_iters, NodeChain &nc) {
+  void *args[] = {(void *)&ctrl, (void *)&words, (void *)&max_iters};
+  return nc.kernel((const void *)while_init_kernel, dim3(1), dim3(1), 0, args);
 }
 
 int saxpy_grid(int64_t n, int unroll) {
@@ -143,13 +138,6 @@ cudaError_t launch_saxpy(const SaxpyArgs &a, int unroll, cudaStream_t s) {
     case 8: saxpy_kernel<8><<<grid, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fill_u32(unsigned int *p, unsigned int v, int64_t n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
-  fill_u32_kernel<<<grid, 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 

@@ -900,24 +900,42 @@ int stencil_rows_blocks_per_sm(int n_noise, int mirror, int cps) {
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_stencil(const StencilArgs &sa, int grid, int block, size_t smem, cudaStream_t s) {
-  cudaError_t e = stencil_prepare();
-  if (e != cudaSuccess) return e;
-  StencilArgs a = sa;
+// The kernel of a stencil launch and its final arguments (the prefix's op pattern filled in);
+// nullptr if the launch shape does not match the kernel it selects.
+static const void *stencil_launch_fn(StencilArgs &a, int block, size_t smem) {
   a.pre_pattern = op_pattern(a.pre, a.npre, &a.pre_pattern_t);
-  void *args[] = {(void *)&a};
   if (a.rows_kernel) {
     const int nn = count_noise_ops(a.pre, a.npre);
     if (!stencil_rows_eligible(a.halo, a.nsuf, a.msuf, nn) || block != kRowsBlock ||
         smem != stencil_rows_smem_bytes() || a.tile_w != kRowsStrip || a.box_w != kRowsBoxW ||
         a.box_h != kRowsChunk || a.tile_h < 1)
-      return cudaErrorInvalidValue;
-    return cudaLaunchKernel(stencil_rows_fn(nn, a.mpre, a.rows_cps), dim3(grid), dim3(block), args, smem, s);
+      return nullptr;
+    return stencil_rows_fn(nn, a.mpre, a.rows_cps);
   }
   if (block != kBlock || smem > 200 * 1024 || stencil_tile_width(a.tile_w) != a.tile_w ||
       (a.halo != 0 && a.halo != 2))
-    return cudaErrorInvalidValue;
-  return cudaLaunchKernel(stencil_fn(a.tile_w, a.halo), dim3(grid), dim3(block), args, smem, s);
+    return nullptr;
+  return stencil_fn(a.tile_w, a.halo);
+}
+
+cudaError_t launch_stencil(const StencilArgs &sa, int grid, int block, size_t smem, cudaStream_t s) {
+  cudaError_t e = stencil_prepare();
+  if (e != cudaSuccess) return e;
+  StencilArgs a = sa;
+  const void *fn = stencil_launch_fn(a, block, smem);
+  if (!fn) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t stencil_node(const StencilArgs &sa, int grid, int block, size_t smem, NodeChain &nc) {
+  cudaError_t e = stencil_prepare();
+  if (e != cudaSuccess) return e;
+  StencilArgs a = sa;  // copied into the node's parameters by cudaGraphAddKernelNode
+  const void *fn = stencil_launch_fn(a, block, smem);
+  if (!fn) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&a};
+  return nc.kernel(fn, dim3(grid), dim3(block), smem, args);
 }
 
 cudaError_t encode_u8_map(CUtensorMap *map, const void *base, int64_t W, int64_t H, int64_t D, int64_t pitch,

@@ -1696,21 +1696,14 @@ mrw_status build_while_plan(Launch &L, const Program &p, const ImgGeom &geo, con
     src = dst;
   }
   CU(stencil_prepare());
-  cudaStream_t cs;
-  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  // the graph is built node by node (no stream capture)
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaGraphCreate(&graph, 0);
   // init: reset the counter, the changed flag and the status word
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaError_t e1 = launch_while_init(wp->ctrl, wp->words, (unsigned long long)p.while_max, cs);
-    cudaGraph_t g2 = nullptr;
-    e = cudaStreamEndCapture(cs, &g2);
-    if (e == cudaSuccess) e = e1;
-  }
-  cudaGraphNode_t init_node = nullptr;
-  size_t nn = 1;
-  if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &init_node, &nn);
+  NodeChain top;
+  top.g = graph;
+  if (e == cudaSuccess) e = while_init_node(wp->ctrl, wp->words, (unsigned long long)p.while_max, top);
+  cudaGraphNode_t init_node = top.last;
   cudaGraphConditionalHandle handle{};
   cudaGraph_t bodyg = nullptr;
   if (e == cudaSuccess)
@@ -1726,27 +1719,23 @@ mrw_status build_while_plan(Launch &L, const Program &p, const ImgGeom &geo, con
     if (e == cudaSuccess) bodyg = cp.conditional.phGraph_out[0];
   }
   // body: the groups A -> B, then a := b where changed, then the control kernel
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e1 = cudaSuccess;
-    for (size_t gi = 0; e1 == cudaSuccess && gi < prep.size(); ++gi) {
+    NodeChain body;
+    body.g = bodyg;
+    for (size_t gi = 0; e == cudaSuccess && gi < prep.size(); ++gi) {
       const Prepared &pr = prep[gi];
       if (pr.stencil) {
-        e1 = cudaMemsetAsync(pr.queue, 0, sizeof(unsigned int), cs);
-        if (e1 == cudaSuccess) e1 = launch_stencil(pr.sa, pr.grid, pr.block, pr.smem, cs);
+        e = body.memset32(pr.queue, 0u, 1);
+        if (e == cudaSuccess) e = stencil_node(pr.sa, pr.grid, pr.block, pr.smem, body);
       } else {
-        e1 = launch_chain(pr.ca, pr.n_noise, pr.cs.unroll, pr.cs.grid, pr.cs.block, cs);
+        e = chain_node(pr.ca, pr.n_noise, pr.cs.unroll, pr.cs.grid, pr.cs.block, body);
       }
     }
-    if (e1 == cudaSuccess) e1 = launch_compare_copy(wp->B, wp->A, geo.rows, (int32_t)geo.W, P, wp->words, L.sms, cs);
-    if (e1 == cudaSuccess) e1 = launch_while_control(wp->ctrl, wp->words, handle, cs);
-    cudaGraph_t g3 = nullptr;
-    e = cudaStreamEndCapture(cs, &g3);
-    if (e == cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = compare_copy_node(wp->B, wp->A, geo.rows, (int32_t)geo.W, P, wp->words, L.sms, body);
+    if (e == cudaSuccess) e = while_control_node(wp->ctrl, wp->words, handle, body);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&wp->exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
-  cudaStreamDestroy(cs);
   if (e != cudaSuccess) return cuda_fail(e, "building the WHILE_CHANGED loop graph");
   return MRW_OK;
 }
@@ -2726,18 +2715,18 @@ mrw_status build_batch_plan(Launch &L, const Program &p, const uint8_t *in_arena
     smems.push_back(s.smem);
     src = dst;
   }
-  // one graph: reset the counters, then the persistent launches
+  // one graph, built node by node: reset the counters, then the persistent launches
   cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(unsigned int) * (gs.size() + 1), cs);
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  NodeChain nc;
+  nc.g = graph;
+  if (e == cudaSuccess) e = nc.memset32(bp->counters, 0u, gs.size() + 1);
   for (size_t gi = 0; e == cudaSuccess && gi < launches.size(); ++gi)
-    e = launch_stencil(launches[gi], grids[gi], blocks[gi], smems[gi], cs);
-  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-  if (e == cudaSuccess) e = e2;
+    e = stencil_node(launches[gi], grids[gi], blocks[gi], smems[gi], nc);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
-  if (e != cudaSuccess) return cuda_fail(e, "capturing the batched launch");
+  if (e != cudaSuccess) return cuda_fail(e, "building the batched launch graph");
   return MRW_OK;
 }
 

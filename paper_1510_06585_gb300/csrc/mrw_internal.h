@@ -99,6 +99,40 @@ struct ChainArgs {
   ChainOp ops[kMaxChainOps];
 };
 
+// A linear chain of CUDA graph nodes built through the graph API (each added node depends on the
+// previous one). Plans that are replayed as graphs are built this way rather than by stream capture:
+// while a stream of the process is capturing, another thread's device-wide synchronisation fails and
+// invalidates the capture, so building by capture would break callers on other threads.
+struct NodeChain {
+  cudaGraph_t g = nullptr;
+  cudaGraphNode_t last = nullptr;
+  cudaError_t kernel(const void *func, dim3 grid, dim3 block, size_t smem, void **args) {
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(func);
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = (unsigned int)smem;
+    kp.kernelParams = args;
+    cudaGraphNode_t n = nullptr;
+    const cudaError_t e = cudaGraphAddKernelNode(&n, g, last ? &last : nullptr, last ? 1 : 0, &kp);
+    if (e == cudaSuccess) last = n;
+    return e;
+  }
+  cudaError_t memset32(void *dst, unsigned int v, size_t count) {
+    cudaMemsetParams mp = {};
+    mp.dst = dst;
+    mp.value = v;
+    mp.elementSize = 4;
+    mp.width = count;
+    mp.height = 1;
+    mp.pitch = 0;
+    cudaGraphNode_t n = nullptr;
+    const cudaError_t e = cudaGraphAddMemsetNode(&n, g, last ? &last : nullptr, last ? 1 : 0, &mp);
+    if (e == cudaSuccess) last = n;
+    return e;
+  }
+};
+
 // Accumulator sets of the in-kernel MapReduce finish, and the largest grid of a chain launch.
 constexpr int kChainSlots = 64;
 constexpr int kMaxChainGrid = 1 << 22;
@@ -107,6 +141,8 @@ constexpr int kMaxChainGrid = 1 << 22;
 int chain_blocks_per_sm(int n_noise, bool mirror, int unroll, int block);
 // n_noise: number of OP_NOISE entries (<= kMaxNoisePerGroup); unroll in {1, 2, 4, 8}.
 cudaError_t launch_chain(const ChainArgs &a, int n_noise, int unroll, int grid, int block, cudaStream_t s);
+// The same launch appended to a graph (no programmatic dependency there).
+cudaError_t chain_node(const ChainArgs &a, int n_noise, int unroll, int grid, int block, NodeChain &nc);
 // The MapReduce finish of a chain launch with a workspace: one CTA that sums the kChainSlots sets of
 // `partials` into red[0, nout) and zeroes them; enqueue it right after that launch on the same stream.
 cudaError_t launch_chain_finish(unsigned long long *partials, unsigned long long *red, int nout, cudaStream_t s);
@@ -172,7 +208,10 @@ int stencil_tile_width(int requested);
 // Shared-memory bytes the stencil kernel needs for a tile shape.
 size_t stencil_smem_bytes(int tile_h, int tile_w, int halo);
 cudaError_t launch_stencil(const StencilArgs &a, int grid, int block, size_t smem, cudaStream_t s);
-// Set the kernel's shared-memory limit; call once before capturing a launch into a graph.
+// The same launch appended to a graph.
+cudaError_t stencil_node(const StencilArgs &a, int grid, int block, size_t smem, NodeChain &nc);
+// Set the kernels' shared-memory limits on the current device (once per device; also before a
+// launch is added to a graph as a node).
 cudaError_t stencil_prepare();
 // Allocation-free batched launch: the tile counter, status word, tensor maps and instance tables
 // live in a file-scope device array of k_stencil.cu (up to kNoAllocMaxInstances instances).
@@ -247,15 +286,14 @@ struct SaxpyArgs {
 };
 cudaError_t launch_saxpy(const SaxpyArgs &a, int unroll, cudaStream_t s);
 int saxpy_grid(int64_t n, int unroll);
-cudaError_t launch_fill_u32(unsigned int *p, unsigned int v, int64_t n, cudaStream_t s);
-
-// WHILE_CHANGED loops: a := b where they differ and *changed := 1 if any byte differed; the
-// control kernel counts the run and sets the WHILE node's condition (changed && iter < max).
-cudaError_t launch_compare_copy(const uint8_t *b, uint8_t *a, int64_t rows, int32_t W, int64_t pitch,
-                                unsigned int *changed, int sms, cudaStream_t s);
-cudaError_t launch_while_control(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, cudaStream_t s);
-// words[0] (changed flag) and words[1] (body status word) are zeroed with the counter.
-cudaError_t launch_while_init(LoopCtrl *ctrl, unsigned int *words, unsigned long long max_iters, cudaStream_t s);
+// WHILE_CHANGED loops, as graph nodes: a := b where they differ and *changed := 1 if any byte
+// differed; the control kernel counts the run and sets the WHILE node's condition
+// (changed && iter < max); the init kernel zeroes the counter, words[0] (the changed flag) and
+// words[1] (the body's status word).
+cudaError_t compare_copy_node(const uint8_t *b, uint8_t *a, int64_t rows, int32_t W, int64_t pitch,
+                              unsigned int *changed, int sms, NodeChain &nc);
+cudaError_t while_control_node(LoopCtrl *ctrl, unsigned int *changed, cudaGraphConditionalHandle h, NodeChain &nc);
+cudaError_t while_init_node(LoopCtrl *ctrl, unsigned int *words, unsigned long long max_iters, NodeChain &nc);
 
 // ------------------------------------------------------------------------------------------
 // Pointwise groups with user-defined stages, compiled at run time (jit.cpp)
