@@ -241,8 +241,10 @@ void mrw_node_release(mrw_node_t n);
  *     (nfft, 65536) or (65536), dense rows, 16-byte aligned device pointers; y = the stages applied
  *     to every row of x in order; y may
  *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
- *     transforms in one launch (a cluster of 8 CTAs per row, the data on chip between transforms);
- *     FUSE_NONE runs one launch per transform.
+ *     transforms in one launch (a cluster of CTAs per row, the data on chip between transforms);
+ *     FUSE_NONE runs one launch per transform. Rows run on clusters of 8 CTAs (two per SM);
+ *     cfg->ctas_per_sm 3 asks for clusters of 16 CTAs instead (three per SM, where the device allows
+ *     that cluster size; faster only for about 16-21 rows).
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with
  * mrw_future_release). `cfg` may be NULL (tuned or default configuration). A call that repeats

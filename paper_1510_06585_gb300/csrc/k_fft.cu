@@ -345,7 +345,256 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
   }
 }
 
+// ---- Clusters of 16 CTAs; the transposes are bulk copies between the CTAs' shared memory ----
+//
+// CTA r of a row's cluster owns the 16 columns b in [16 r, 16 r + 16) of V for the column
+// transforms and the 16 rows k1 in [16 r, 16 r + 16) of the result for the row transforms. Its two
+// 32 KB buffers hold 16 lines of 256 values in the line layout li(l, p); after a column phase the
+// CTA rewrites its values in the send layout, where the 2 KB block d holds what CTA d's row phase
+// needs from it, and 16 bulk copies (cp.async.bulk shared::cluster, completing on the receiver's
+// mbarrier) deliver block d into CTA d's other buffer, at the sender's slot: exactly the line
+// layout of the receiver's 16 rows. No thread waits on a remote load; one cluster barrier per
+// transform makes sure every receive buffer is free before the copies start. With 70 KB of shared
+// memory and 256 threads a CTA, three CTAs share an SM.
+namespace c16 {
+constexpr int kC = 256 / kFft16Cluster;      // 16 lines per CTA
+constexpr int kT = 256;                      // 16 threads per line, all lines at once
+constexpr int kE = kN / kFft16Cluster;       // 4096 values per CTA
+constexpr uint32_t kBlock = kE / kFft16Cluster * 8;  // 2 KB per destination
+constexpr uint32_t kPolls = 1u << 22;
+static_assert(kC == 16 && kT == 16 * kC, "one round of 16 lines");
+
+struct Smem {
+  float2 buf[2][kE];
+  float2 tw[16][16];   // W_256^(t k), stored at [k][t] (forward sign)
+  float2 tlo[kC][16];  // W_N^(b l),    b = 16 r + j
+  float2 thi[kC][16];  // W_N^(16 b h)
+  uint64_t bar[2];     // receive barrier of each buffer
+};
+
+// Line layout: position p of line l is in 16-value block p >> 4 (the sending CTA's rank, for
+// received values), row l of it, column (p ^ l ^ (p >> 4)) & 15: every access pattern below
+// touches 16 distinct bank pairs per half warp.
+__device__ __forceinline__ int li(int l, int p) { return ((p >> 4) << 8) | (l << 4) | ((p ^ l ^ (p >> 4)) & 15); }
+// Send layout of CTA `rank`: the value for destination d, row k of d's lines, from this CTA's line j.
+__device__ __forceinline__ int si(int d, int k, int j, int rank) { return (d << 8) | (k << 4) | ((j ^ k ^ rank) & 15); }
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t remote(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; ++i)
+    if (try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Pass 2 inside line l of buffer d: the pass-1 results v (y[k1] in v[dft16_slot(k1)]) to positions
+// 16 k1 + t, then the 16-point DFT of positions 16 t .. 16 t + 15 left in v.
+template <int S>
+__device__ __forceinline__ void pass2_line(float2 *d, int l, int t, float2 (&v)[16]) {
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) d[li(l, 16 * k1 + t)] = v[dft16_slot(k1)];
+  __syncwarp();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) v[n2] = d[li(l, 16 * t + n2)];
+  __syncwarp();
+  dft16<S>(v);
+}
+
+// One transform of the row: column phase on buffer w, exchange into buffer 1 - w of every CTA of
+// the cluster, row phase there. Every thread of every CTA calls it. `parity` holds the next
+// completion parity of each receive barrier; `failed` records a wait that gave up.
+template <int S>
+__device__ void transform16(Smem &sm, int w, int rank, float scale, uint32_t &parity, uint32_t polls, bool &failed) {
+  const int tid = threadIdx.x, t = tid & 15, l = tid >> 4;
+  float2 *d = sm.buf[w];
+  float2 *e = sm.buf[1 - w];
+  float2 v[16];
+  // column transform of line l (column b = 16 rank + l of V) over its 256 positions a
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = d[li(l, t + 16 * m)];
+  pass1<S>(v, t, sm.tw);
+  __syncwarp();
+  pass2_line<S>(d, l, t, v);
+  __syncthreads();  // every line has read its values: the buffer takes the send layout
+  {
+    const float2 lo = conj_if(sm.tlo[l][t], S < 0);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2)  // result k1 = t + 16 k2 goes to CTA k2, row t there
+      d[si(k2, t, l, rank)] = cmul(v[dft16_slot(k2)], cmul(lo, conj_if(sm.thi[l][k2], S < 0)));
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the copies read these values
+  __syncthreads();
+  if (tid == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&sm.bar[1 - w])),
+                 "r"((uint32_t)kE * 8u)
+                 : "memory");
+  // every CTA's receive buffer is free (its previous contents were read or stored) and armed
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (tid < kFft16Cluster) {  // thread k sends block k to CTA k, into the slot of this CTA
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        "cp.async.bulk.commit_group;" ::"r"(remote(e + (rank << 8), (uint32_t)tid)),
+        "r"(saddr(d + (tid << 8))), "r"(kBlock), "r"(remote(&sm.bar[1 - w], (uint32_t)tid))
+        : "memory");
+  }
+  const uint32_t par = (parity >> (1 - w)) & 1u;
+  if (!wait_bounded(&sm.bar[1 - w], par, polls)) failed = true;
+  parity ^= 1u << (1 - w);
+  if (tid < kFft16Cluster) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncthreads();  // the sends have been read: buffer w may be refilled
+  // row transform of line l (row k1 = 16 rank + l) over its 256 positions b
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = e[li(l, t + 16 * m)];
+  pass1<S>(v, t, sm.tw);
+  __syncwarp();
+  pass2_line<S>(e, l, t, v);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const float2 x = v[dft16_slot(k2)];
+    e[li(l, t + 16 * k2)] = make_float2(x.x * scale, x.y * scale);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kT, 3) fft16_kernel(const __grid_constant__ FftArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int64_t cl = blockIdx.x / kFft16Cluster, ncl = gridDim.x / kFft16Cluster;
+  const uint32_t polls = a.wait_polls ? a.wait_polls - 1 : kPolls;
+
+  for (int i = tid; i < 256; i += kT) {
+    const int k = i >> 4, t = i & 15;
+    float sn, cs;
+    sincospif((float)(t * k) / 128.f, &sn, &cs);
+    sm.tw[k][t] = make_float2(cs, -sn);
+    const uint32_t b = (uint32_t)(kC * rank + k);  // line k, index t
+    sincospif((float)((b * (uint32_t)t) & (kN - 1)) / (float)(kN / 2), &sn, &cs);
+    sm.tlo[k][t] = make_float2(cs, -sn);
+    sincospif((float)((b * 16u * (uint32_t)t) & (kN - 1)) / (float)(kN / 2), &sn, &cs);
+    sm.thi[k][t] = make_float2(cs, -sn);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&sm.bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&sm.bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster.sync();  // the barriers exist before any CTA sends
+
+  uint32_t parity = 0;
+  bool failed = false;
+  for (int64_t f = cl; f < a.nfft; f += ncl) {
+    // columns [16 rank, 16 rank + 16) of row f: value (a, j) = x[256 a + 16 rank + j] to line j,
+    // position a; two values per 16-byte load, all of a thread's loads in flight first
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kC * rank);
+      constexpr int kLoads = kE / 2 / kT;
+      float4 q[kLoads];
+#pragma unroll
+      for (int i = 0; i < kLoads; ++i) {
+        const int u = tid + i * kT;
+        q[i] = __ldcs(src + 128 * (u >> 3) + (u & 7));
+      }
+#pragma unroll
+      for (int i = 0; i < kLoads; ++i) {
+        const int u = tid + i * kT, ar = u >> 3, j = 2 * (u & 7);
+        sm.buf[0][li(j, ar)] = make_float2(q[i].x, q[i].y);
+        sm.buf[0][li(j + 1, ar)] = make_float2(q[i].z, q[i].w);
+      }
+    }
+    __syncthreads();
+    int w = 0;
+    for (int s = 0; s < a.nsteps; ++s) {
+      const float scale = a.sign[s] > 0 ? 1.f : 1.f / (float)kN;
+      if (a.sign[s] > 0) transform16<1>(sm, w, rank, scale, parity, polls, failed);
+      else transform16<-1>(sm, w, rank, scale, parity, polls, failed);
+      w = 1 - w;
+    }
+    // line l of buffer w is row k1 = 16 rank + l of the result: y[k1 + 256 p] for positions p,
+    // the 16 lines of one position being 128 contiguous bytes; two values per 16-byte store
+    {
+      float4 *dst = reinterpret_cast<float4 *>(a.out + f * kN + kC * rank);
+      const float2 *b = sm.buf[w];
+#pragma unroll 4
+      for (int u = tid; u < kE / 2; u += kT) {
+        const int p = u >> 3, l = 2 * (u & 7);
+        const float2 lo = b[li(l, p)], hi = b[li(l + 1, p)];
+        __stcs(dst + 128 * p + (u & 7), make_float4(lo.x, lo.y, hi.x, hi.y));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < kFft16Cluster) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (failed && a.status) *(volatile unsigned int *)a.status = 1u;
+  cluster.sync();  // no CTA leaves while a copy into it could still be under way
+}
+}  // namespace c16
+
 }  // namespace
+
+size_t fft16_smem_bytes() { return sizeof(c16::Smem); }
+
+int fft16_max_clusters() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  int n = 0;
+  if (cudaFuncSetAttribute(c16::fft16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(c16::Smem)) == cudaSuccess &&
+      cudaFuncSetAttribute(c16::fft16_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(c16::kT);
+    cfg.gridDim = dim3(kFft16Cluster);
+    cfg.dynamicSmemBytes = sizeof(c16::Smem);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kFft16Cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)c16::fft16_kernel, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  cached = n;
+  return n;
+}
+
+cudaError_t launch_fft16(const FftArgs &a, int clusters, cudaStream_t s) {
+  if (a.nsteps < 1 || a.nsteps > kFftMaxSteps || a.nfft < 1 || clusters < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(c16::fft16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(c16::Smem));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(c16::fft16_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(c16::kT);
+  cfg.gridDim = dim3(kFft16Cluster * clusters);
+  cfg.dynamicSmemBytes = sizeof(c16::Smem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kFft16Cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, c16::fft16_kernel, a);
+}
 
 size_t fft_smem_bytes() { return sizeof(FftSmem); }
 

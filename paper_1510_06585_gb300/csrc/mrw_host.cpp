@@ -2111,7 +2111,15 @@ mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *
   return MRW_OK;
 }
 
-mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg) {
+// Which FFT kernel runs the rows: clusters of 8 CTAs (two per SM) unless cfg.ctas_per_sm is 3,
+// which asks for clusters of 16 CTAs (three per SM; where the device allows that cluster size). The
+// 16-CTA kernel spreads a row over twice the CTAs but fewer rows run at once; measured on GB300 for a
+// forward and inverse pair it is 8 % faster at 16-21 rows and slower at every other row count tried
+// (240 against 191 us at 256 rows), so it is the tuner's to choose, not the default.
+bool fft_use16(const mrw_config &cfg, int64_t) { return cfg.ctas_per_sm == 3 && fft16_max_clusters() > 0; }
+
+mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
+                       unsigned int *status, bool *used_status) {
   View vx, vy;
   TRY(validate_fft_args(args, nargs, &vx, &vy));
   const bool inplace = args[0].data == args[1].data;
@@ -2123,11 +2131,14 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
   } else {
     TRY(resolve(L, vy, false, true, &dy, &pp));
   }
-  const int maxc = fft_max_clusters();
+  const int max16 = fft_use16(cfg, vx.rows) ? fft16_max_clusters() : 0;
+  const int maxc = max16 > 0 ? max16 : fft_max_clusters();
   if (maxc < 1) return fail(MRW_ERR_UNSUPPORTED, "a %d-CTA cluster with %zu bytes of shared memory does not fit",
                             kFftCluster, fft_smem_bytes());
   FftArgs a{};
   a.nfft = vx.rows;
+  a.status = max16 > 0 ? status : nullptr;
+  if (a.status) *used_status = true;
   const int clusters = (int)std::min<int64_t>(a.nfft, maxc);
   const int per = cfg.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
   a.in = (const float2 *)dx;
@@ -2135,7 +2146,8 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
   for (size_t i = 0; i < p.fft.size(); i += per) {
     a.nsteps = (int32_t)std::min<size_t>(per, p.fft.size() - i);
     for (int k = 0; k < a.nsteps; ++k) a.sign[k] = p.fft[i + k];
-    CU(launch_fft(a, clusters, L.stream));
+    if (max16 > 0) CU(launch_fft16(a, clusters, L.stream));
+    else CU(launch_fft(a, clusters, L.stream));
     a.in = (const float2 *)dy;  // later launches continue in place on y
   }
   return MRW_OK;
@@ -2194,7 +2206,7 @@ mrw_status enqueue(Launch &L, const Program &p, const mrw_buffer *args, int narg
     case F_IMAGE: TRY(enqueue_image(L, p, args, nargs, cfg, status, used_status)); break;
     case F_NBODY: TRY(enqueue_nbody(L, p, args, nargs, cfg)); break;
     case F_SAXPY: TRY(enqueue_saxpy(L, p, args, nargs, cfg)); break;
-    case F_FFT: TRY(enqueue_fft(L, p, args, nargs, cfg)); break;
+    case F_FFT: TRY(enqueue_fft(L, p, args, nargs, cfg, status, used_status)); break;
     default: return fail(MRW_ERR_INVALID_ARG, "empty tree");
   }
   TRY(copy_back(L));
@@ -2927,8 +2939,10 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     View vx, vy;
     TRY(validate_fft_args(args, nargs, &vx, &vy));
     const int per = c.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
-    o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"cluster\":" << kFftCluster
-      << ",\"smem\":" << fft_smem_bytes() << ",\"launches\":[";
+    const bool c16 = fft_use16(c, vx.rows);
+    o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"cluster\":"
+      << (c16 ? kFft16Cluster : kFftCluster) << ",\"smem\":" << (c16 ? fft16_smem_bytes() : fft_smem_bytes())
+      << ",\"launches\":[";
     for (size_t i = 0; i < p.fft.size(); i += per) {
       o << (i ? "," : "") << "[";
       for (size_t k = i; k < std::min(p.fft.size(), i + per); ++k) o << (k > i ? "," : "") << (p.fft[k] > 0 ? "\"fft\"" : "\"ifft\"");

@@ -240,11 +240,21 @@ struct FftArgs {
   int64_t nfft;
   int32_t nsteps;                // transforms applied in order, 1..kFftMaxSteps
   int32_t sign[kFftMaxSteps];    // +1 forward (kernel e^(-2 pi i nk/N)), -1 inverse (e^(+...), / N)
+  unsigned int *status;          // 16-CTA kernel: set to 1 if a bounded wait gave up (may be null)
+  uint32_t wait_polls;           // 16-CTA kernel: 0 = default bound; N > 0: give up after N - 1 polls
 };
 size_t fft_smem_bytes();
 // Clusters that can be resident at once (0 if the launch configuration is not possible).
 int fft_max_clusters();
 cudaError_t launch_fft(const FftArgs &a, int clusters, cudaStream_t s);
+// Clusters of 16 CTAs (a non-portable cluster size), 16 of the 256 columns per CTA in 32 KB, and a
+// second 32 KB buffer per CTA that the other CTAs fill with bulk copies between shared memories (the
+// transposes of the four-step decomposition): three CTAs per SM. 0 clusters if the device cannot
+// run them.
+constexpr int kFft16Cluster = 16;
+size_t fft16_smem_bytes();
+int fft16_max_clusters();
+cudaError_t launch_fft16(const FftArgs &a, int clusters, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // N-body

@@ -1,5 +1,5 @@
 """GPU parity of the FFT stages (Section 4, FFT pipelined with its inversion) against the FP64
-oracle: rows of 65,536 complex float32 values, one cluster of 8 CTAs per row.
+oracle: rows of 65,536 complex float32 values, one cluster of 8 or 16 CTAs per row.
 
 Tolerance: normwise relative error per row <= 1e-5. A float32 transform of 2^16 points goes
 through 16 radix-2-equivalent levels, each adding a rounding error of a few units of 2^-24 to the
@@ -80,7 +80,7 @@ def test_one_row_and_plan():
     x = inputs.fft_signals(1, N, seed=2)[0]  # a 1-D buffer is one row
     assert F.rel_error(run(tree_of(["ifft"]), x), F.ifft_rows(x)) <= TOL
     d = M.plan_describe(M.loop(M.stage("fft"), 9), [torch.from_numpy(inputs.fft_signals(2, N)).cuda()] * 2)
-    assert d["family"] == "fft" and [len(l) for l in d["launches"]] == [8, 1] and d["cluster"] in (4, 8)
+    assert d["family"] == "fft" and [len(l) for l in d["launches"]] == [8, 1] and d["cluster"] in (4, 8, 16)
 
 
 def test_rejects_bad_shapes_and_types():
@@ -106,3 +106,22 @@ def test_full_size_256_rows_128_mb():
     M.execute(tree_of(["fft"]), [xd, yd]).wait(120000)
     rows = [0, 37, 128, 255]
     assert F.rel_error(yd.cpu().numpy()[rows], F.fft_rows(x[rows])) <= TOL
+
+
+@pytest.mark.parametrize("cps,cluster", [(0, 8), (2, 8), (3, 16)])
+def test_both_cluster_kernels_on_every_row_count(cps, cluster):
+    # clusters of 8 CTAs (distributed-shared-memory pulls; the default) and of 16 CTAs (bulk copies
+    # between the CTAs' shared memory), chosen by the configuration, on row counts below, at and
+    # above the number of clusters that run at once, in place and out of place, and through a
+    # 3-transform fused launch
+    cfg = M.config(ctas_per_sm=cps)
+    for nfft in (1, 5, 23, 40):
+        x = inputs.fft_signals(nfft, N, seed=nfft)
+        d = M.plan_describe(tree_of(["fft"]), [torch.from_numpy(x).cuda()] * 2, cfg)
+        assert d["cluster"] == cluster
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        M.execute(tree_of(["fft", "ifft", "fft"]), [xd, yd], cfg).wait(60000)
+        assert F.rel_error(yd.cpu().numpy(), F.pipeline(x, ["fft", "ifft", "fft"])) <= TOL, nfft
+        M.execute(tree_of(["ifft"]), [xd, xd], cfg).wait(60000)
+        assert F.rel_error(xd.cpu().numpy(), F.ifft_rows(x)) <= TOL, nfft
