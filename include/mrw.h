@@ -242,9 +242,11 @@ void mrw_node_release(mrw_node_t n);
  *     to every row of x in order; y may
  *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
  *     transforms in one launch (a cluster of CTAs per row, the data on chip between transforms);
- *     FUSE_NONE runs one launch per transform. Rows run on clusters of 8 CTAs (two per SM);
- *     cfg->ctas_per_sm 3 asks for clusters of 16 CTAs instead (three per SM, where the device allows
- *     that cluster size; faster only for about 16-21 rows).
+ *     FUSE_NONE runs one launch per transform. Rows run on clusters of 8 CTAs: by default with
+ *     two CTAs per SM, and, when there are more rows than such clusters run at once, with three per
+ *     SM (the values a CTA holds across the exchange wait in tensor memory instead of registers).
+ *     cfg->ctas_per_sm 2 asks for the first form, 4 for the second, 3 for clusters of 16 CTAs
+ *     (three per SM, where the device allows that cluster size; faster only for about 16-21 rows).
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with
  * mrw_future_release). `cfg` may be NULL (tuned or default configuration). A call that repeats

@@ -28,6 +28,8 @@
 //       j * 256 + ((a & 0xF0) | ((a ^ (a >> 4) ^ j) & 15))
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "mrw_internal.h"
 
 namespace cg = cooperative_groups;
@@ -52,6 +54,7 @@ struct FftSmem {
   float2 tw[16][16];     // W_256^(t k), stored at [k][t] (forward sign)
   float2 tlo[kCols][16]; // W_N^(b l),      b = kCols r + j, l < 16
   float2 thi[kCols][16]; // W_N^(16 b h),   h < 16
+  uint32_t tmem;         // TMEM address of the CTA's 128 columns (the TMEM-stash form)
 };
 
 __device__ __forceinline__ int ab(int a, int j) { return a * kCols + (j ^ ((a ^ (a >> 4)) & 15)); }
@@ -129,6 +132,28 @@ __device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
   return v;
 }
 
+// Tensor memory (TMEM) as a per-thread stash: 32 consecutive 32-bit columns of the thread's lane
+// (lane 32 (warp % 4) + laneid, the lanes a warp may reach) hold the 16 complex values of one round.
+// tcgen05.st reads its registers when it issues; tcgen05.wait::st / wait::ld wait for the
+// thread's own stores / loads to complete.
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float2 (&v)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+               ::"r"(taddr), "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[1].x)), "r"(__float_as_uint(v[1].y)), "r"(__float_as_uint(v[2].x)), "r"(__float_as_uint(v[2].y)), "r"(__float_as_uint(v[3].x)), "r"(__float_as_uint(v[3].y)), "r"(__float_as_uint(v[4].x)), "r"(__float_as_uint(v[4].y)), "r"(__float_as_uint(v[5].x)), "r"(__float_as_uint(v[5].y)), "r"(__float_as_uint(v[6].x)), "r"(__float_as_uint(v[6].y)), "r"(__float_as_uint(v[7].x)), "r"(__float_as_uint(v[7].y)), "r"(__float_as_uint(v[8].x)), "r"(__float_as_uint(v[8].y)), "r"(__float_as_uint(v[9].x)), "r"(__float_as_uint(v[9].y)), "r"(__float_as_uint(v[10].x)), "r"(__float_as_uint(v[10].y)), "r"(__float_as_uint(v[11].x)), "r"(__float_as_uint(v[11].y)), "r"(__float_as_uint(v[12].x)), "r"(__float_as_uint(v[12].y)), "r"(__float_as_uint(v[13].x)), "r"(__float_as_uint(v[13].y)), "r"(__float_as_uint(v[14].x)), "r"(__float_as_uint(v[14].y)), "r"(__float_as_uint(v[15].x)), "r"(__float_as_uint(v[15].y))
+               : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float2 (&v)[16]) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr)
+               : "memory");
+  // the registers are defined only once the load has completed: every use depends on the wait
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+}
+
 // Index of line position p in shared memory: a column of the AB layout, or a row of the BA one.
 template <bool AB>
 __device__ __forceinline__ int line_idx(int line, int p) {
@@ -180,8 +205,11 @@ __device__ __forceinline__ void pass2_in_place(float2 *d, int line, int t, float
 
 // One transform (sign S) of this CTA's part: column transforms (input layout AB or BA), the
 // exchange, row transforms into layout BA. Every thread of every CTA of the cluster calls it.
-template <int S, bool AB>
-__device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, float scale) {
+// Between the exchange's pulls and the barrier after them, the pass-1 results wait in registers, or
+// with TM in the thread's TMEM columns from `ta` on (32 per round), which frees the registers for a
+// third CTA per SM.
+template <int S, bool AB, bool TM>
+__device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, float scale, uint32_t ta) {
   const int tid = threadIdx.x;
   const int t = tid & 15, g = tid >> 4;  // line group: 32 lines at a time
   float2 *d = sm.d;
@@ -200,50 +228,56 @@ __device__ void transform(FftSmem &sm, cg::cluster_group &cluster, int rank, flo
   }
   cluster.sync();  // every part's column transforms are done
   constexpr int kRounds = kCols / (kThreads / 16);
-  if constexpr (AB) {
-    // pull the values of this CTA's rows k1 = kCols rank + line for b = t + 16 m from their owners;
-    // in layout AB a half warp's 16 values of one line are contiguous in the owner's memory
-    float2 v[kRounds][16];
+  // AB: pull the values of this CTA's rows k1 = kCols rank + line for b = t + 16 m from their
+  // owners; in layout AB a half warp's 16 values of one line are contiguous in the owner's memory.
+  // BA: one value b of 32 consecutive lines is contiguous: a warp pulls for 32 lines at one position
+  // tq (one line per lane), so each pull reads whole 32-byte sectors of the owner's memory; the
+  // pass-1 results then go to this CTA's rows and pass 2 reads them back with the usual mapping
+  // (half a warp per line) after a barrier.
+  const int tq = AB ? t : tid / kLines, gq = AB ? g : tid % kLines;
+  auto pull = [&](int rd, float2 (&v)[16]) {
+    const int k1 = kCols * rank + gq + rd * (AB ? kThreads / 16 : kLines);
 #pragma unroll
-    for (int rd = 0; rd < kRounds; ++rd) {
-      const int k1 = kCols * rank + g + rd * (kThreads / 16);
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int b = t + 16 * m;  // owned by rank b / kCols = m / (kCols / 16)
-        v[rd][m] = ld_cluster(cluster_addr(d + ab(k1, b & (kCols - 1)), (uint32_t)(m / (kCols / 16))));
-      }
-      pass1<S>(v[rd], t, sm.tw);
+    for (int m = 0; m < 16; ++m) {
+      const int b = tq + 16 * m;  // owned by rank b / kCols = m / (kCols / 16)
+      const float2 *src = AB ? d + ab(k1, b & (kCols - 1)) : d + ba(b & (kCols - 1), k1);
+      v[m] = ld_cluster(cluster_addr(src, (uint32_t)(m / (kCols / 16))));
     }
-    cluster.sync();  // every pull is done: the parts may be overwritten
-#pragma unroll
-    for (int rd = 0; rd < kRounds; ++rd) {
-      const int line = g + rd * (kThreads / 16);
-      pass2<S, false>(d, line, t, v[rd], [&](int, float2 x) { return make_float2(x.x * scale, x.y * scale); });
-    }
-  } else {
-    // In layout BA one value b of 32 consecutive lines is contiguous: a warp pulls for 32 lines at
-    // one position tq (one line per lane), so each pull reads whole 32-byte sectors of the owner's
-    // memory; the pass-1 results then go to this CTA's rows and pass 2 reads them back with the
-    // usual mapping (half a warp per line) after a barrier.
-    const int tq = tid / kLines, gq = tid % kLines;
-    float2 v[kRounds][16];
-#pragma unroll
-    for (int rd = 0; rd < kRounds; ++rd) {
-      const int k1 = kCols * rank + gq + rd * kLines;
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int b = tq + 16 * m;  // owned by rank b / 64 = m / 4
-        v[rd][m] = ld_cluster(cluster_addr(d + ba(b & (kCols - 1), k1), (uint32_t)(m / (kCols / 16))));
-      }
-      pass1<S>(v[rd], tq, sm.tw);
-    }
-    cluster.sync();  // every pull is done: the parts may be overwritten
-#pragma unroll
-    for (int rd = 0; rd < kRounds; ++rd) {
+    pass1<S>(v, tq, sm.tw);
+  };
+  auto finish = [&](int rd, float2 (&v)[16]) {
+    if constexpr (AB) {
+      pass2<S, false>(d, g + rd * (kThreads / 16), t, v, [&](int, float2 x) { return make_float2(x.x * scale, x.y * scale); });
+    } else {
       const int line = gq + rd * kLines;
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) d[ba(line, 16 * k1 + tq)] = v[rd][dft16_slot(k1)];
+      for (int k1 = 0; k1 < 16; ++k1) d[ba(line, 16 * k1 + tq)] = v[dft16_slot(k1)];
     }
+  };
+  if constexpr (TM) {
+#pragma unroll 1
+    for (int rd = 0; rd < kRounds; ++rd) {
+      float2 v[16];
+      pull(rd, v);
+      tm_st16(ta + 32u * (uint32_t)rd, v);
+    }
+    tm_wait_st();
+    cluster.sync();  // every pull is done: the parts may be overwritten
+#pragma unroll 1
+    for (int rd = 0; rd < kRounds; ++rd) {
+      float2 v[16];
+      tm_ld16(ta + 32u * (uint32_t)rd, v);
+      finish(rd, v);
+    }
+  } else {
+    float2 v[kRounds][16];
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) pull(rd, v[rd]);
+    cluster.sync();  // every pull is done: the parts may be overwritten
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) finish(rd, v[rd]);
+  }
+  if constexpr (!AB) {
     __syncthreads();
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) pass2_in_place<S, false>(d, g + rd * (kThreads / 16), t, scale);
@@ -267,7 +301,10 @@ __device__ __forceinline__ void fft_io_slot(int e, int *r, int *j) {
   }
 }
 
-__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, kMinBlocks)
+// TM: the exchange's pass-1 results wait in TMEM (128 columns per CTA, allocated by warp 0 for the
+// kernel's lifetime), so a thread needs at most 80 registers and three CTAs share an SM.
+template <bool TM>
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, TM ? 3 : kMinBlocks)
     fft_cluster_kernel(const __grid_constant__ FftArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   FftSmem &sm = *reinterpret_cast<FftSmem *>(smem_raw);
@@ -275,6 +312,19 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
   const int64_t cl = blockIdx.x / kFftCluster, ncl = gridDim.x / kFftCluster;
+  static_assert(!TM || (kFftCluster == 8 && kThreads == 256), "the TMEM stash is laid out for 8 warps");
+  if constexpr (TM) {
+    // three CTAs of 128 columns fit the SM's 512 (shared memory and registers admit no fourth), so
+    // the allocation never waits
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&sm.tmem)),
+                   "r"(128u)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
 
   // twiddle tables: W_M^e = (cos(2 pi e / M), -sin(2 pi e / M)), exact integer exponents
   for (int e = tid; e < 256; e += kThreads) {
@@ -293,25 +343,33 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     sm.thi[j][l] = make_float2(cs, -sn);
   }
   __syncthreads();
+  uint32_t ta = 0;  // this thread's TMEM columns: lane 32 (warp % 4) + laneid, 64 columns per warp half
+  if constexpr (TM) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int w = tid >> 5;
+    ta = sm.tmem + ((uint32_t)(32 * (w & 3)) << 16) + 64u * (uint32_t)(w >> 2);
+  }
 
   for (int64_t f = cl; f < a.nfft; f += ncl) {
     // this CTA's columns of row f: element (a, j) = x[256 a + kCols rank + j], layout AB; two values
     // per 16-byte load
     const float4 *src = reinterpret_cast<const float4 *>(a.in + f * kN + kCols * rank);
-    {
-      // all of the thread's 16 loads in flight before the first store to shared memory
-      constexpr int kLoads = kUnits / kThreads;
-      float4 q[kLoads];
+    // all of the thread's 16 loads in flight before the first store to shared memory (8 at a time
+    // in the 80-register TM form)
+    constexpr int kLoads = kUnits / kThreads, kBatch = TM ? 8 : kLoads;
+#pragma unroll 1
+    for (int i0 = 0; i0 < kLoads; i0 += kBatch) {
+      float4 q[kBatch];
 #pragma unroll
-      for (int i = 0; i < kLoads; ++i) {
+      for (int i = 0; i < kBatch; ++i) {
         int r, j;
-        fft_io_slot(tid + i * kThreads, &r, &j);
+        fft_io_slot(tid + (i0 + i) * kThreads, &r, &j);
         q[i] = __ldcs(src + 128 * r + (j >> 1));
       }
 #pragma unroll
-      for (int i = 0; i < kLoads; ++i) {
+      for (int i = 0; i < kBatch; ++i) {
         int r, j;
-        fft_io_slot(tid + i * kThreads, &r, &j);
+        fft_io_slot(tid + (i0 + i) * kThreads, &r, &j);
         sm.d[ab(r, j)] = make_float2(q[i].x, q[i].y);
         sm.d[ab(r, j + 1)] = make_float2(q[i].z, q[i].w);
       }
@@ -320,11 +378,11 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     for (int s = 0; s < a.nsteps; ++s) {
       const float scale = a.sign[s] > 0 ? 1.f : 1.f / (float)kN;
       if (s == 0) {
-        if (a.sign[0] > 0) transform<1, true>(sm, cluster, rank, scale);
-        else transform<-1, true>(sm, cluster, rank, scale);
+        if (a.sign[0] > 0) transform<1, true, TM>(sm, cluster, rank, scale, ta);
+        else transform<-1, true, TM>(sm, cluster, rank, scale, ta);
       } else {
-        if (a.sign[s] > 0) transform<1, false>(sm, cluster, rank, scale);
-        else transform<-1, false>(sm, cluster, rank, scale);
+        if (a.sign[s] > 0) transform<1, false, TM>(sm, cluster, rank, scale, ta);
+        else transform<-1, false, TM>(sm, cluster, rank, scale, ta);
       }
     }
     // the cluster's next row: its 256 segments of this CTA's kCols columns (8 kCols bytes each) into L2
@@ -343,7 +401,22 @@ __global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 
     }
     __syncthreads();
   }
+  if constexpr (TM) {
+    // every thread's TMEM loads completed (tcgen05.wait::ld in tm_ld16) before the columns go back
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem), "r"(128u) : "memory");
+  }
 }
+
+// Residency of the TM form: an empty kernel of the same cluster shape, block size, register budget
+// (three CTAs per SM) and shared memory. The occupancy calculator counts a kernel that uses tcgen05
+// instructions as one CTA per SM, but the hardware places three of these per SM (measured: 51
+// clusters resident at once, the figure below, and a 52nd queues); what limits them is shared
+// memory and registers, and their 3 x 128 TMEM columns fit the SM's 512.
+__global__ void __cluster_dims__(kFftCluster, 1, 1) __launch_bounds__(kThreads, 3) fft_tm_residency_probe() {}
 
 // ---- Clusters of 16 CTAs; the transposes are bulk copies between the CTAs' shared memory ----
 //
@@ -598,11 +671,14 @@ cudaError_t launch_fft16(const FftArgs &a, int clusters, cudaStream_t s) {
 
 size_t fft_smem_bytes() { return sizeof(FftSmem); }
 
-int fft_max_clusters() {
-  static int cached = -1;
-  if (cached >= 0) return cached;
-  if (cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(FftSmem)) != cudaSuccess) {
+int fft_max_clusters(bool tm) {
+  static std::atomic<int> cached[2] = {-1, -1};
+  std::atomic<int> &c = cached[tm ? 1 : 0];
+  if (c.load() >= 0) return c.load();
+  const void *fn = tm ? (const void *)fft_cluster_kernel<true> : (const void *)fft_cluster_kernel<false>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FftSmem)) != cudaSuccess ||
+      (tm && cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)) {
     cudaGetLastError();
     return 0;
   }
@@ -611,20 +687,33 @@ int fft_max_clusters() {
   cfg.gridDim = dim3(kFftCluster);
   cfg.dynamicSmemBytes = sizeof(FftSmem);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (void *)fft_cluster_kernel, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
+  if (tm && n > 0) {
+    // the probe's residency, provided the kernel's own registers admit three CTAs per SM
+    cudaFuncAttributes fa{};
+    int np = 0;
+    const void *probe = (const void *)fft_tm_residency_probe;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.numRegs * kThreads * 3 <= 65536 &&
+        cudaFuncSetAttribute(probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FftSmem)) == cudaSuccess &&
+        cudaFuncSetAttribute(probe, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&np, probe, &cfg) == cudaSuccess && np > n)
+      n = np;
   }
-  cached = n;
+  cudaGetLastError();
+  c.store(n);
   return n;
 }
 
-cudaError_t launch_fft(const FftArgs &a, int clusters, cudaStream_t s) {
+cudaError_t launch_fft(const FftArgs &a, int clusters, bool tm, cudaStream_t s) {
   if (a.nsteps < 1 || a.nsteps > kFftMaxSteps || a.nfft < 1 || clusters < 1) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(FftSmem));
+  const void *fn = tm ? (const void *)fft_cluster_kernel<true> : (const void *)fft_cluster_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FftSmem));
+  if (e == cudaSuccess && tm)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  fft_cluster_kernel<<<dim3(kFftCluster * clusters), dim3(kThreads), sizeof(FftSmem), s>>>(a);
+  if (tm) fft_cluster_kernel<true><<<dim3(kFftCluster * clusters), dim3(kThreads), sizeof(FftSmem), s>>>(a);
+  else fft_cluster_kernel<false><<<dim3(kFftCluster * clusters), dim3(kThreads), sizeof(FftSmem), s>>>(a);
   return cudaGetLastError();
 }
 

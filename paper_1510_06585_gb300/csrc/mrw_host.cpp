@@ -2111,12 +2111,22 @@ mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *
   return MRW_OK;
 }
 
-// Which FFT kernel runs the rows: clusters of 8 CTAs (two per SM) unless cfg.ctas_per_sm is 3,
-// which asks for clusters of 16 CTAs (three per SM; where the device allows that cluster size). The
-// 16-CTA kernel spreads a row over twice the CTAs but fewer rows run at once; measured on GB300 for a
-// forward and inverse pair it is 8 % faster at 16-21 rows and slower at every other row count tried
-// (240 against 191 us at 256 rows), so it is the tuner's to choose, not the default.
-bool fft_use16(const mrw_config &cfg, int64_t) { return cfg.ctas_per_sm == 3 && fft16_max_clusters() > 0; }
+// Which FFT kernel runs the rows. Clusters of 8 CTAs keep the exchange's values in registers (two
+// CTAs per SM; 36 clusters at once on GB300) or in TMEM (three per SM; 51 clusters). A row takes
+// as long or longer with three CTAs per SM, so the TMEM form pays only when the rows outnumber the
+// register form's resident clusters: measured for a forward and inverse pair, 5-12 % faster from 40
+// rows on (181 against 192 us at 256 rows) and up to 17 % slower at 8-36 rows. The default takes
+// the TMEM form exactly when nfft exceeds the register form's residency; cfg.ctas_per_sm 2 asks
+// for the register form, 4 for the TMEM form and 3 for clusters of 16 CTAs (three per SM, where the
+// device allows that cluster size; 8 % faster than the default only at 16-21 rows).
+enum FftForm { FFT_REG, FFT_TMEM, FFT_C16 };
+FftForm fft_form(const mrw_config &cfg, int64_t nfft) {
+  if (cfg.ctas_per_sm == 3 && fft16_max_clusters() > 0) return FFT_C16;
+  if (cfg.ctas_per_sm == 2) return FFT_REG;
+  const int tm = fft_max_clusters(true), reg = fft_max_clusters(false);
+  if (cfg.ctas_per_sm == 4) return tm > 0 ? FFT_TMEM : FFT_REG;
+  return tm > reg && nfft > reg ? FFT_TMEM : FFT_REG;
+}
 
 mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
                        unsigned int *status, bool *used_status) {
@@ -2131,8 +2141,10 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
   } else {
     TRY(resolve(L, vy, false, true, &dy, &pp));
   }
-  const int max16 = fft_use16(cfg, vx.rows) ? fft16_max_clusters() : 0;
-  const int maxc = max16 > 0 ? max16 : fft_max_clusters();
+  const FftForm form = fft_form(cfg, vx.rows);
+  const bool tm = form == FFT_TMEM;
+  const int max16 = form == FFT_C16 ? fft16_max_clusters() : 0;
+  const int maxc = max16 > 0 ? max16 : fft_max_clusters(tm);
   if (maxc < 1) return fail(MRW_ERR_UNSUPPORTED, "a %d-CTA cluster with %zu bytes of shared memory does not fit",
                             kFftCluster, fft_smem_bytes());
   FftArgs a{};
@@ -2147,7 +2159,7 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
     a.nsteps = (int32_t)std::min<size_t>(per, p.fft.size() - i);
     for (int k = 0; k < a.nsteps; ++k) a.sign[k] = p.fft[i + k];
     if (max16 > 0) CU(launch_fft16(a, clusters, L.stream));
-    else CU(launch_fft(a, clusters, L.stream));
+    else CU(launch_fft(a, clusters, tm, L.stream));
     a.in = (const float2 *)dy;  // later launches continue in place on y
   }
   return MRW_OK;
@@ -2939,10 +2951,12 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     View vx, vy;
     TRY(validate_fft_args(args, nargs, &vx, &vy));
     const int per = c.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
-    const bool c16 = fft_use16(c, vx.rows);
+    const FftForm form = fft_form(c, vx.rows);
+    const bool c16 = form == FFT_C16, tm = form == FFT_TMEM;
     o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"cluster\":"
       << (c16 ? kFft16Cluster : kFftCluster) << ",\"smem\":" << (c16 ? fft16_smem_bytes() : fft_smem_bytes())
-      << ",\"launches\":[";
+      << ",\"tmem\":" << (tm ? "true" : "false") << ",\"clusters_resident\":"
+      << (c16 ? fft16_max_clusters() : fft_max_clusters(tm)) << ",\"launches\":[";
     for (size_t i = 0; i < p.fft.size(); i += per) {
       o << (i ? "," : "") << "[";
       for (size_t k = i; k < std::min(p.fft.size(), i + per); ++k) o << (k > i ? "," : "") << (p.fft[k] > 0 ? "\"fft\"" : "\"ifft\"");

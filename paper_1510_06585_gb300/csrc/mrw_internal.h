@@ -244,9 +244,10 @@ struct FftArgs {
   uint32_t wait_polls;           // 16-CTA kernel: 0 = default bound; N > 0: give up after N - 1 polls
 };
 size_t fft_smem_bytes();
-// Clusters that can be resident at once (0 if the launch configuration is not possible).
-int fft_max_clusters();
-cudaError_t launch_fft(const FftArgs &a, int clusters, cudaStream_t s);
+// Clusters that can be resident at once (0 if the launch configuration is not possible). tm: the
+// form that keeps the exchange's values in TMEM instead of registers (three CTAs per SM).
+int fft_max_clusters(bool tm);
+cudaError_t launch_fft(const FftArgs &a, int clusters, bool tm, cudaStream_t s);
 // Clusters of 16 CTAs (a non-portable cluster size), 16 of the 256 columns per CTA in 32 KB, and a
 // second 32 KB buffer per CTA that the other CTAs fill with bulk copies between shared memories (the
 // transposes of the four-step decomposition): three CTAs per SM. 0 clusters if the device cannot

@@ -108,17 +108,29 @@ def test_full_size_256_rows_128_mb():
     assert F.rel_error(yd.cpu().numpy()[rows], F.fft_rows(x[rows])) <= TOL
 
 
-@pytest.mark.parametrize("cps,cluster", [(0, 8), (2, 8), (3, 16)])
-def test_both_cluster_kernels_on_every_row_count(cps, cluster):
-    # clusters of 8 CTAs (distributed-shared-memory pulls; the default) and of 16 CTAs (bulk copies
-    # between the CTAs' shared memory), chosen by the configuration, on row counts below, at and
-    # above the number of clusters that run at once, in place and out of place, and through a
-    # 3-transform fused launch
+def test_tmem_form_runs_more_clusters_at_once():
+    # the form that parks the exchange's values in tensor memory exists to fit three CTAs per SM
+    x = torch.zeros(2, N, dtype=torch.complex64, device="cuda")
+    reg = M.plan_describe(tree_of(["fft"]), [x, x], M.config(ctas_per_sm=2))
+    tm = M.plan_describe(tree_of(["fft"]), [x, x], M.config(ctas_per_sm=4))
+    assert not reg["tmem"] and tm["tmem"] and tm["clusters_resident"] > reg["clusters_resident"] > 0
+
+
+@pytest.mark.parametrize("cps,cluster,tmem", [(0, 8, None), (2, 8, False), (3, 16, False), (4, 8, True)])
+def test_every_cluster_kernel_on_every_row_count(cps, cluster, tmem):
+    # clusters of 8 CTAs with the exchange's values in registers (two CTAs per SM) or in tensor
+    # memory (three per SM; the default once the rows outnumber the register form's resident
+    # clusters, tmem None here), and clusters of 16 CTAs (bulk copies between the CTAs' shared
+    # memory), chosen by the configuration, on row counts below, at and above the number of
+    # clusters that run at once, in place and out of place, and through a 3-transform fused launch
     cfg = M.config(ctas_per_sm=cps)
-    for nfft in (1, 5, 23, 40):
+    for nfft in (1, 5, 23, 40, 61):
         x = inputs.fft_signals(nfft, N, seed=nfft)
-        d = M.plan_describe(tree_of(["fft"]), [torch.from_numpy(x).cuda()] * 2, cfg)
-        assert d["cluster"] == cluster
+        xs = [torch.from_numpy(x).cuda()] * 2
+        d = M.plan_describe(tree_of(["fft"]), xs, cfg)
+        want_tm = tmem if tmem is not None else \
+            nfft > M.plan_describe(tree_of(["fft"]), xs, M.config(ctas_per_sm=2))["clusters_resident"]
+        assert d["cluster"] == cluster and d["tmem"] == want_tm and d["clusters_resident"] > 0
         xd = torch.from_numpy(x).cuda()
         yd = torch.empty_like(xd)
         M.execute(tree_of(["fft", "ifft", "fft"]), [xd, yd], cfg).wait(60000)
