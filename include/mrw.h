@@ -241,12 +241,15 @@ void mrw_node_release(mrw_node_t n);
  *     (nfft, 65536) or (65536), dense rows, 16-byte aligned device pointers; y = the stages applied
  *     to every row of x in order; y may
  *     be x itself (in place) but must not overlap it otherwise. FUSE_ALL runs up to 8 consecutive
- *     transforms in one launch (a cluster of CTAs per row, the data on chip between transforms);
- *     FUSE_NONE runs one launch per transform. Rows run on clusters of 8 CTAs: by default with
- *     two CTAs per SM, and, when there are more rows than such clusters run at once, with three per
- *     SM (the values a CTA holds across the exchange wait in tensor memory instead of registers).
- *     cfg->ctas_per_sm 2 asks for the first form, 4 for the second, 3 for clusters of 16 CTAs
- *     (three per SM, where the device allows that cluster size; faster only for about 16-21 rows).
+ *     transforms in one launch (the values stay on chip or in L2 between transforms, so HBM sees
+ *     each input read once and each output written once); FUSE_NONE runs one launch per
+ *     transform. Up to as many rows as clusters of 8 CTAs run at once (36 on GB300), each row runs
+ *     on such a cluster, two CTAs per SM; with more rows, a persistent grid splits every row into
+ *     work items (16 columns or 16 lines of its 256 x 256 four-step matrix) whose values wait
+ *     between phases in an L2-resident ring (a few tens of MB of device scratch per call; see
+ *     mrw_fft_schedule_check). cfg->ctas_per_sm 1 asks for that form, 2 for the cluster form, 4
+ *     for clusters of 8 with the exchange's values in tensor memory (three CTAs per SM), 3 for
+ *     clusters of 16 CTAs (where the device allows that cluster size).
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
  * it enqueues work on `stream` and returns a future in *out (release it with
  * mrw_future_release). `cfg` may be NULL (tuned or default configuration). A call that repeats
@@ -330,6 +333,17 @@ mrw_status mrw_future_elapsed_ms(mrw_future_t f, float *ms);
  * and the errors of mrw_future_wait. May be called more than once, before mrw_future_release. */
 mrw_status mrw_future_result(mrw_future_t f, void *host_dst, size_t bytes);
 void mrw_future_release(mrw_future_t f);
+
+/* The ticket schedule of the L2-ring FFT form (Section 4, FFT pipelined with its inversion, run as
+ * a persistent grid; the paper has no such schedule): for nfft rows, nsteps transforms per launch
+ * (1..8) and a grid of `ctas` CTAs, plans the slices and the ring, then checks on the host that every
+ * work item (phase, row, 16-column or 16-line part) has exactly one ticket and that every item
+ * waits only for items with smaller tickets, so that the persistent grid cannot deadlock. If `out`
+ * is not NULL it receives 5 values: rows per slice, steps between a row's phases, ring rows (of
+ * 512 KB each), grid CTAs and tickets. Launches nothing and needs no GPU. Errors:
+ * MRW_ERR_UNSUPPORTED (no schedule: nfft < 1, nsteps outside 1..8, ctas < 1, or more than 2^31
+ * tickets), MRW_ERR_CONSTRAINT (the check failed). */
+mrw_status mrw_fft_schedule_check(int64_t nfft, int32_t nsteps, int32_t ctas, int64_t *out);
 
 /* Describe the plan the executor would run for (root, args, cfg) as a JSON string: the fused
  * kernel groups, their stages, launch shapes and partitions. Writes at most `cap` bytes

@@ -30,6 +30,7 @@
 
 #include <atomic>
 
+#include "fft_ops.cuh"
 #include "mrw_internal.h"
 
 namespace cg = cooperative_groups;
@@ -45,9 +46,6 @@ constexpr int kUnits = kN / kFftCluster / 2;            // 16-byte units of a CT
 constexpr int kMinBlocks = kFftCluster == 4 ? 1 : 2;    // CTAs per SM the registers are budgeted for
 static_assert(kFftCluster == 4 || kFftCluster == 8, "clusters of 4 or 8 CTAs");
 static_assert(kCols % kLines == 0 && kUnits % kThreads == 0, "whole rounds");
-constexpr float kC8 = 0.92387953251128675613f;  // cos(pi / 8)
-constexpr float kS8 = 0.38268343236508977173f;  // sin(pi / 8)
-constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1 / 2)
 
 struct FftSmem {
   float2 d[kN / kFftCluster];  // this CTA's part of the row (128 or 64 KB)
@@ -60,58 +58,7 @@ struct FftSmem {
 __device__ __forceinline__ int ab(int a, int j) { return a * kCols + (j ^ ((a ^ (a >> 4)) & 15)); }
 __device__ __forceinline__ int ba(int j, int a) { return j * 256 + ((a & 0xF0) | ((a ^ (a >> 4) ^ j) & 15)); }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 conj_if(float2 a, bool c) { return c ? make_float2(a.x, -a.y) : a; }
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by -s i (the 4-point kernel W_4^s): s = +1 (forward) maps (x, y) to (y, -x)
-template <int S>
-__device__ __forceinline__ float2 rot(float2 a) {
-  return S > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
-}
-
-// 4-point DFT of (a, b, c, d) with kernel W_4^(S n k), results in place (index k).
-template <int S>
-__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
-  const float2 z0 = add(a, c), z1 = sub(a, c), z2 = add(b, d), z3 = rot<S>(sub(b, d));
-  a = add(z0, z2);
-  c = sub(z0, z2);
-  b = add(z1, z3);
-  d = sub(z1, z3);
-}
-
-// W_16^(S e) for the exponents the 4 x 4 split needs.
-template <int S>
-__device__ __forceinline__ float2 w16(int e) {
-  const float s = (float)S;
-  switch (e) {
-    case 1: return make_float2(kC8, -s * kS8);
-    case 2: return make_float2(kR2, -s * kR2);
-    case 3: return make_float2(kS8, -s * kC8);
-    case 4: return make_float2(0.f, -s);
-    case 6: return make_float2(-kR2, -s * kR2);
-    case 9: return make_float2(-kC8, s * kS8);
-    default: return make_float2(1.f, 0.f);
-  }
-}
-
-// 16-point DFT with kernel W_16^(S n k) of v[n]; the result X[k] is left in v[4 (k % 4) + k / 4].
-template <int S>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
-#pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) dft4<S>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);  // over n1
-  // now v[4 k1 + n2] = y[k1][n2]; twiddle W_16^(n2 k1)
-#pragma unroll
-  for (int k1 = 1; k1 < 4; ++k1)
-#pragma unroll
-    for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<S>(n2 * k1));
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);  // over n2
-}
-
-__device__ __forceinline__ int dft16_slot(int k) { return 4 * (k & 3) + (k >> 2); }
+using namespace fftk;  // complex arithmetic and the 16-point DFT
 
 // Shared-memory window address of this CTA's `p` in the CTA of the cluster with rank `rank`, and an
 // 8-byte load from such an address (distributed shared memory).

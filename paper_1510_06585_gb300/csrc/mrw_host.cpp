@@ -2111,21 +2111,64 @@ mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *
   return MRW_OK;
 }
 
-// Which FFT kernel runs the rows. Clusters of 8 CTAs keep the exchange's values in registers (two
-// CTAs per SM; 36 clusters at once on GB300) or in TMEM (three per SM; 51 clusters). A row takes
-// as long or longer with three CTAs per SM, so the TMEM form pays only when the rows outnumber the
-// register form's resident clusters: measured for a forward and inverse pair, 5-12 % faster from 40
-// rows on (181 against 192 us at 256 rows) and up to 17 % slower at 8-36 rows. The default takes
-// the TMEM form exactly when nfft exceeds the register form's residency; cfg.ctas_per_sm 2 asks
-// for the register form, 4 for the TMEM form and 3 for clusters of 16 CTAs (three per SM, where the
-// device allows that cluster size; 8 % faster than the default only at 16-21 rows).
-enum FftForm { FFT_REG, FFT_TMEM, FFT_C16 };
+// Which FFT kernel runs the rows. Clusters of 8 CTAs keep a row on chip, the exchange's values in
+// registers (two CTAs per SM; 36 clusters at once on GB300) or in TMEM (three per SM; 51
+// clusters); the L2-ring form splits each row's phases into work items of a persistent grid and
+// exchanges the values through an L2-resident ring. Every row of a cluster form runs at once up to
+// the clusters' residency, and there the register form's row is the shortest (26 against 31 us for
+// a forward and inverse pair of 16 rows); beyond it the L2-ring form is the fastest measured (48 us
+// at 64 rows, 159 at 256, 307 at 512, against 50, 182 and 360 for the TMEM form). The default takes
+// the L2-ring form exactly when nfft exceeds the register form's residency. cfg.ctas_per_sm 1 asks
+// for the L2-ring form, 2 for the register form, 4 for the TMEM form and 3 for clusters of 16 CTAs
+// (three per SM, where the device allows that cluster size).
+enum FftForm { FFT_REG, FFT_TMEM, FFT_C16, FFT_L2 };
 FftForm fft_form(const mrw_config &cfg, int64_t nfft) {
+  if (cfg.ctas_per_sm == 1 && fft_l2_ctas_per_sm() > 0) return FFT_L2;
   if (cfg.ctas_per_sm == 3 && fft16_max_clusters() > 0) return FFT_C16;
   if (cfg.ctas_per_sm == 2) return FFT_REG;
   const int tm = fft_max_clusters(true), reg = fft_max_clusters(false);
   if (cfg.ctas_per_sm == 4) return tm > 0 ? FFT_TMEM : FFT_REG;
+  if (nfft > reg && fft_l2_ctas_per_sm() > 0) return FFT_L2;
   return tm > reg && nfft > reg ? FFT_TMEM : FFT_REG;
+}
+
+// The L2-ring form: one workspace (the ring and the completion counters, sized for the largest
+// launch) serves every launch of the chain in stream order.
+mrw_status enqueue_fft_l2(Launch &L, const Program &p, const float2 *dx, float2 *dy, int64_t nfft, int per,
+                          unsigned int *status, bool *used_status) {
+  const int ctas = fft_l2_ctas_per_sm() * L.sms;
+  std::vector<FftL2Plan> plans;
+  size_t ring = 0, counters = 0;
+  for (size_t i = 0; i < p.fft.size(); i += per) {
+    FftL2Plan pl{};
+    if (!fft_l2_plan(nfft, (int)std::min<size_t>(per, p.fft.size() - i), ctas, &pl))
+      return fail(MRW_ERR_UNSUPPORTED, "%lld FFT rows do not fit the L2-ring schedule", (long long)nfft);
+    ring = std::max(ring, pl.ring_bytes);
+    counters = std::max(counters, pl.counter_bytes);
+    plans.push_back(pl);
+  }
+  void *ws = nullptr;
+  const size_t ring_padded = (ring + 255) / 256 * 256;
+  TRY(L.alloc(&ws, ring_padded + counters));
+  FftL2Args a{};
+  a.in = dx;
+  a.out = dy;
+  a.ring = (float2 *)ws;
+  a.done = (unsigned int *)((char *)ws + ring_padded);
+  a.status = status;
+  a.wait_polls = test_wait_polls();
+  if (status) *used_status = true;
+  for (size_t i = 0, c = 0; i < p.fft.size(); i += per, ++c) {
+    const FftL2Plan &pl = plans[c];
+    a.sc = pl.sc;
+    a.ring_rows = pl.ring_rows;
+    a.ticket = a.done + pl.sc.nfft * pl.sc.P;
+    a.nsteps = pl.sc.P - 1;
+    for (int k = 0; k < a.nsteps; ++k) a.sign[k] = p.fft[i + k];
+    CU(launch_fft_l2(a, pl.ctas, L.stream));
+    a.in = dy;  // later launches continue in place on y
+  }
+  return MRW_OK;
 }
 
 mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int nargs, const mrw_config &cfg,
@@ -2142,6 +2185,8 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
     TRY(resolve(L, vy, false, true, &dy, &pp));
   }
   const FftForm form = fft_form(cfg, vx.rows);
+  const int per = cfg.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
+  if (form == FFT_L2) return enqueue_fft_l2(L, p, (const float2 *)dx, (float2 *)dy, vx.rows, per, status, used_status);
   const bool tm = form == FFT_TMEM;
   const int max16 = form == FFT_C16 ? fft16_max_clusters() : 0;
   const int maxc = max16 > 0 ? max16 : fft_max_clusters(tm);
@@ -2152,7 +2197,6 @@ mrw_status enqueue_fft(Launch &L, const Program &p, const mrw_buffer *args, int 
   a.status = max16 > 0 ? status : nullptr;
   if (a.status) *used_status = true;
   const int clusters = (int)std::min<int64_t>(a.nfft, maxc);
-  const int per = cfg.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
   a.in = (const float2 *)dx;
   a.out = (float2 *)dy;
   for (size_t i = 0; i < p.fft.size(); i += per) {
@@ -2952,11 +2996,24 @@ mrw_status describe(const Program &p, const mrw_buffer *args, int nargs, const m
     TRY(validate_fft_args(args, nargs, &vx, &vy));
     const int per = c.fusion == MRW_FUSE_ALL ? kFftMaxSteps : 1;
     const FftForm form = fft_form(c, vx.rows);
-    const bool c16 = form == FFT_C16, tm = form == FFT_TMEM;
-    o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"cluster\":"
-      << (c16 ? kFft16Cluster : kFftCluster) << ",\"smem\":" << (c16 ? fft16_smem_bytes() : fft_smem_bytes())
-      << ",\"tmem\":" << (tm ? "true" : "false") << ",\"clusters_resident\":"
-      << (c16 ? fft16_max_clusters() : fft_max_clusters(tm)) << ",\"launches\":[";
+    const bool c16 = form == FFT_C16, tm = form == FFT_TMEM, l2 = form == FFT_L2;
+    o << "{\"family\":\"fft\",\"n\":" << kFftN << ",\"nfft\":" << vx.rows << ",\"form\":\""
+      << (l2 ? "l2" : (c16 ? "c16" : (tm ? "tmem" : "reg"))) << "\"";
+    if (l2) {
+      FftL2Plan pl{};
+      const int ctas = fft_l2_ctas_per_sm() * sms;
+      if (!fft_l2_plan(vx.rows, (int)std::min<size_t>(per, p.fft.size()), ctas, &pl))
+        return fail(MRW_ERR_UNSUPPORTED, "%lld FFT rows do not fit the L2-ring schedule", (long long)vx.rows);
+      o << ",\"cluster\":1,\"smem\":" << fft_l2_smem_bytes() << ",\"tmem\":false,\"ctas\":" << pl.ctas
+        << ",\"ctas_per_sm\":" << fft_l2_ctas_per_sm() << ",\"slice_rows\":" << pl.sc.G << ",\"lag_steps\":" << pl.sc.L
+        << ",\"ring_rows\":" << pl.ring_rows << ",\"schedule_ok\":"
+        << (fft_l2_schedule_ok(pl.sc, pl.ring_rows) ? "true" : "false");
+    } else {
+      o << ",\"cluster\":" << (c16 ? kFft16Cluster : kFftCluster) << ",\"smem\":"
+        << (c16 ? fft16_smem_bytes() : fft_smem_bytes()) << ",\"tmem\":" << (tm ? "true" : "false")
+        << ",\"clusters_resident\":" << (c16 ? fft16_max_clusters() : fft_max_clusters(tm));
+    }
+    o << ",\"launches\":[";
     for (size_t i = 0; i < p.fft.size(); i += per) {
       o << (i ? "," : "") << "[";
       for (size_t k = i; k < std::min(p.fft.size(), i + per); ++k) o << (k > i ? "," : "") << (p.fft[k] > 0 ? "\"fft\"" : "\"ifft\"");
@@ -3094,6 +3151,23 @@ mrw_status model_predict(mrw_model *m, const float *feat, int *best) {
 }  // namespace
 
 extern "C" {
+
+mrw_status mrw_fft_schedule_check(int64_t nfft, int32_t nsteps, int32_t ctas, int64_t *out) {
+  FftL2Plan pl{};
+  if (!fft_l2_plan(nfft, nsteps, ctas, &pl))
+    return fail(MRW_ERR_UNSUPPORTED, "no L2-ring schedule for %lld rows, %d transforms, %d CTAs", (long long)nfft,
+                nsteps, ctas);
+  if (out) {
+    out[0] = pl.sc.G;
+    out[1] = pl.sc.L;
+    out[2] = pl.ring_rows;
+    out[3] = pl.ctas;
+    out[4] = fsch_total_tickets(pl.sc);
+  }
+  if (!fft_l2_schedule_ok(pl.sc, pl.ring_rows))
+    return fail(MRW_ERR_CONSTRAINT, "the L2-ring schedule for %lld rows is inconsistent", (long long)nfft);
+  return MRW_OK;
+}
 
 mrw_status mrw_plan_describe(mrw_node_t root, const mrw_buffer *args, int32_t nargs, const mrw_config *cfg,
                              char *buf, int64_t cap, int64_t *needed) {

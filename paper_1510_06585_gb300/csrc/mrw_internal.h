@@ -257,6 +257,47 @@ size_t fft16_smem_bytes();
 int fft16_max_clusters();
 cudaError_t launch_fft16(const FftArgs &a, int clusters, cudaStream_t s);
 
+// The same chains with the four-step transposes exchanged through an L2-resident ring of rows in
+// global memory: a persistent grid of CTAs of 16 kFftL2Block threads claims work items (phase p
+// of row f, kFftL2Block of its columns or lines) from a ticket counter. See k_fft_l2.cu for the
+// ticket order.
+constexpr int kFftL2Block = 16;
+constexpr int kFftL2Items = 256 / kFftL2Block;  // items per row and phase
+struct FftSched {
+  int64_t nfft;     // rows
+  int64_t nslices;  // ceil(nfft / G)
+  int32_t P;        // phases: transforms + 1
+  int32_t G;        // rows per slice
+  int32_t L;        // steps between a slice's consecutive phases (1 <= L <= nslices)
+  int32_t pad;
+};
+struct FftL2Args {
+  const float2 *in;        // nfft rows of kFftN values (16-byte aligned, dense)
+  float2 *out;             // same shape; may equal `in`
+  float2 *ring;            // ring_rows rows of kFftN values (256-byte aligned)
+  unsigned int *done;      // nfft * P completion counters, zeroed by launch_fft_l2
+  unsigned int *ticket;    // == done + nfft * P, zeroed with them
+  unsigned int *status;    // set to 1 if a bounded wait gave up (may be null)
+  FftSched sc;
+  int64_t ring_rows;
+  int32_t nsteps;
+  int32_t sign[kFftMaxSteps];
+  uint32_t wait_polls;     // 0 = default bound; N > 0: give up a wait after N - 1 polls
+};
+struct FftL2Plan {
+  FftSched sc;
+  int64_t ring_rows;
+  int ctas;                // grid size (at most the resident CTAs)
+  size_t ring_bytes;       // ring_rows rows
+  size_t counter_bytes;    // nfft * P + 1 counters
+};
+size_t fft_l2_smem_bytes();
+int fft_l2_ctas_per_sm();  // resident CTAs per SM on the current device (0: cannot launch)
+bool fft_l2_plan(int64_t nfft, int nsteps, int ctas, FftL2Plan *out);
+bool fft_l2_schedule_ok(const FftSched &c, int64_t ring_rows);
+int64_t fsch_total_tickets(const FftSched &c);  // work items of one launch (empty rows included)
+cudaError_t launch_fft_l2(const FftL2Args &a, int ctas, cudaStream_t s);
+
 // ------------------------------------------------------------------------------------------
 // N-body
 // ------------------------------------------------------------------------------------------

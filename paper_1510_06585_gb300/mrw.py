@@ -105,6 +105,8 @@ _SIGS = {
     "mrw_future_elapsed_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
     "mrw_future_result": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "mrw_future_release": (None, [_P]),
+    "mrw_fft_schedule_check": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_int64)]),
     "mrw_plan_describe": (ctypes.c_int, [_P, ctypes.POINTER(mrw_buffer), ctypes.c_int32, ctypes.POINTER(mrw_config),
                                          ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mrw_tune_candidates": (ctypes.c_int, [_P, ctypes.POINTER(mrw_buffer), ctypes.c_int32, ctypes.POINTER(mrw_config),
@@ -375,6 +377,13 @@ def execute_batched(root: Node, in_arena, out_arena, desc, cfg: mrw_config | Non
                                      ctypes.byref(cfg) if cfg is not None else None, stream_handle(stream),
                                      ctypes.byref(out)), "mrw_execute_batched")
     return Future(out)
+
+
+def fft_schedule_check(nfft: int, nsteps: int, ctas: int) -> dict:
+    """Plan and check the L2-ring FFT schedule on the host (mrw_fft_schedule_check)."""
+    out = (ctypes.c_int64 * 5)()
+    check(load().mrw_fft_schedule_check(nfft, nsteps, ctas, out), "mrw_fft_schedule_check")
+    return dict(zip(("slice_rows", "lag_steps", "ring_rows", "ctas", "tickets"), out[:]))
 
 
 def plan_describe(root: Node, args, cfg: mrw_config | None = None) -> str:

@@ -328,3 +328,26 @@ def test_empty_buffers_are_refused_before_any_launch(lib):
             arr[i].memory = mrw.MRW_MEM_HOST
         assert lib.mrw_execute(tree.h, arr, len(args), None, None, ctypes.byref(fut)) == mrw.MRW_ERR_SHAPE
         assert not fut.value
+
+
+def test_fft_ring_schedule_gives_every_item_one_ticket_and_waits_only_backwards(lib):
+    # the persistent FFT grid claims work items in ticket order and waits only for smaller tickets
+    # (checked exhaustively on the host for every plan here); phase p + 1 of a row trails phase p
+    # by about 2.5 grids of tickets, and the ring holds at most (P - 1) L + 3 slices of rows
+    for ctas in (1, 7, 152, 456):
+        for nsteps in (1, 2, 3, 8):
+            for nfft in (1, 2, 5, 36, 37, 83, 256, 1000):
+                r = mrw.fft_schedule_check(nfft, nsteps, ctas)
+                P, G, L = nsteps + 1, r["slice_rows"], r["lag_steps"]
+                slices = -(-nfft // G)
+                assert r["tickets"] == slices * G * 16 * P and r["ctas"] == min(ctas, r["tickets"])
+                assert 1 <= L <= 2 and (L == 2 or slices < 2)
+                assert r["ring_rows"] == min(slices, (P - 1) * L + 3) * G
+                if slices >= 2:
+                    assert 16 * G * L * P >= 2.5 * ctas  # the lag between a row's phases, in tickets
+    with pytest.raises(mrw.MrwError) as e:
+        mrw.fft_schedule_check(0, 2, 152)
+    assert e.value.status == mrw.MRW_ERR_UNSUPPORTED
+    with pytest.raises(mrw.MrwError) as e:
+        mrw.fft_schedule_check(4, 9, 152)
+    assert e.value.status == mrw.MRW_ERR_UNSUPPORTED

@@ -1,5 +1,6 @@
 """GPU parity of the FFT stages (Section 4, FFT pipelined with its inversion) against the FP64
-oracle: rows of 65,536 complex float32 values, one cluster of 8 or 16 CTAs per row.
+oracle: rows of 65,536 complex float32 values, one cluster of 8 or 16 CTAs per row, or work items
+of a persistent grid exchanging through an L2-resident ring.
 
 Tolerance: normwise relative error per row <= 1e-5. A float32 transform of 2^16 points goes
 through 16 radix-2-equivalent levels, each adding a rounding error of a few units of 2^-24 to the
@@ -74,6 +75,9 @@ def test_long_chains_more_rows_than_clusters_in_place_and_host_buffers():
     assert F.rel_error(run(tree_of(["fft"]), x, inplace=True), want) <= TOL
     assert F.rel_error(run(tree_of(["fft"]), x[:3], host=True), want[:3]) <= TOL
     assert F.rel_error(run(tree_of(["fft"]), x[:2], host=True, inplace=True), want[:2]) <= TOL
+    ring = M.config(ctas_per_sm=1)  # the L2-ring form on host buffers, out of place and in place
+    assert F.rel_error(run(tree_of(["fft"]), x[:41], ring, host=True), want[:41]) <= TOL
+    assert F.rel_error(run(tree_of(["ifft", "fft"]), x[:7], ring, host=True, inplace=True), x[:7]) <= TOL
 
 
 def test_one_row_and_plan():
@@ -116,24 +120,59 @@ def test_tmem_form_runs_more_clusters_at_once():
     assert not reg["tmem"] and tm["tmem"] and tm["clusters_resident"] > reg["clusters_resident"] > 0
 
 
-@pytest.mark.parametrize("cps,cluster,tmem", [(0, 8, None), (2, 8, False), (3, 16, False), (4, 8, True)])
-def test_every_cluster_kernel_on_every_row_count(cps, cluster, tmem):
+@pytest.mark.parametrize("cps,form", [(0, None), (1, "l2"), (2, "reg"), (3, "c16"), (4, "tmem")])
+def test_every_kernel_form_on_every_row_count(cps, form):
     # clusters of 8 CTAs with the exchange's values in registers (two CTAs per SM) or in tensor
-    # memory (three per SM; the default once the rows outnumber the register form's resident
-    # clusters, tmem None here), and clusters of 16 CTAs (bulk copies between the CTAs' shared
-    # memory), chosen by the configuration, on row counts below, at and above the number of
-    # clusters that run at once, in place and out of place, and through a 3-transform fused launch
+    # memory (three per SM), clusters of 16 CTAs (bulk copies between the CTAs' shared memory), and
+    # the persistent grid of work items over an L2-resident ring (the default once the rows
+    # outnumber the register form's resident clusters, form None here), chosen by the
+    # configuration, on row counts below, at and above the number of clusters that run at once, in
+    # place and out of place, and through a 3-transform fused launch
     cfg = M.config(ctas_per_sm=cps)
     for nfft in (1, 5, 23, 40, 61):
         x = inputs.fft_signals(nfft, N, seed=nfft)
         xs = [torch.from_numpy(x).cuda()] * 2
         d = M.plan_describe(tree_of(["fft"]), xs, cfg)
-        want_tm = tmem if tmem is not None else \
-            nfft > M.plan_describe(tree_of(["fft"]), xs, M.config(ctas_per_sm=2))["clusters_resident"]
-        assert d["cluster"] == cluster and d["tmem"] == want_tm and d["clusters_resident"] > 0
+        want = form if form is not None else \
+            ("l2" if nfft > M.plan_describe(tree_of(["fft"]), xs, M.config(ctas_per_sm=2))["clusters_resident"] else "reg")
+        assert d["form"] == want, (nfft, d)
+        if want == "l2":
+            assert d["schedule_ok"] and d["ctas"] > 0 and d["ring_rows"] >= d["slice_rows"]
+        else:
+            assert d["cluster"] == (16 if want == "c16" else 8) and d["tmem"] == (want == "tmem")
+            assert d["clusters_resident"] > 0
         xd = torch.from_numpy(x).cuda()
         yd = torch.empty_like(xd)
         M.execute(tree_of(["fft", "ifft", "fft"]), [xd, yd], cfg).wait(60000)
         assert F.rel_error(yd.cpu().numpy(), F.pipeline(x, ["fft", "ifft", "fft"])) <= TOL, nfft
         M.execute(tree_of(["ifft"]), [xd, xd], cfg).wait(60000)
         assert F.rel_error(xd.cpu().numpy(), F.ifft_rows(x)) <= TOL, nfft
+
+
+def test_ring_form_wait_gives_up_and_reports_without_hanging():
+    # A child process runs the L2-ring form with its dependency waits told to give up at once:
+    # items claimed before the items they read have finished give up, the kernel records it in the
+    # status word and runs out its tickets, the future reports it, and the stream stays usable.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r"""
+import os, sys, torch
+sys.path.insert(0, %r)
+from paper_1510_06585_gb300 import mrw as M, inputs
+from oracle import fft as F
+x = inputs.fft_signals(2, 65536, seed=3)
+xd = torch.from_numpy(x).cuda(); yd = torch.empty_like(xd)
+t = M.pipeline(M.stage("fft"), M.stage("ifft"))
+f = M.execute(t, [xd, yd], M.config(ctas_per_sm=1))
+print("status", M.load().mrw_future_wait(f.h, 60000))
+os.environ.pop("MRW_TEST_WAIT_POLLS")
+M.execute(t, [xd, yd], M.config(ctas_per_sm=1)).wait(60000)
+print("after", F.rel_error(yd.cpu().numpy(), x) <= 1e-5)
+""" % root
+    env = dict(os.environ, MRW_TEST_WAIT_POLLS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "status %d" % M.MRW_ERR_DEVICE in r.stdout, r.stdout
+    assert "after True" in r.stdout, r.stdout
