@@ -24,14 +24,30 @@ __device__ __forceinline__ float2 rot(float2 a) {
   return S > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
 
-// 4-point DFT of (a, b, c, d) with kernel W_4^(S n k), results in place (index k).
+// Sums and differences of both parts of a value at once (sm_100+ f32x2 instructions), rounded as
+// the two float32 operations they replace.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long x, y, d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+  return r;
+}
+
+// 4-point DFT of (a, b, c, d) with kernel W_4^(S n k), results in place (index k). The sums and
+// differences are paired instructions; -S i (b - d) is formed directly in its rotated order by two
+// single subtractions, so no register swap is needed.
 template <int S>
 __device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
-  const float2 z0 = add(a, c), z1 = sub(a, c), z2 = add(b, d), z3 = rot<S>(sub(b, d));
-  a = add(z0, z2);
-  c = sub(z0, z2);
-  b = add(z1, z3);
-  d = sub(z1, z3);
+  const float2 z0 = add2(a, c), z1 = sub2(a, c), z2 = add2(b, d);
+  const float2 z3 = S > 0 ? make_float2(b.y - d.y, d.x - b.x) : make_float2(d.y - b.y, b.x - d.x);
+  a = add2(z0, z2);
+  c = sub2(z0, z2);
+  b = add2(z1, z3);
+  d = sub2(z1, z3);
 }
 
 // W_16^(S e) for the exponents the 4 x 4 split needs.
@@ -58,7 +74,8 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 #pragma unroll
   for (int k1 = 1; k1 < 4; ++k1)
 #pragma unroll
-    for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<S>(n2 * k1));
+    for (int n2 = 1; n2 < 4; ++n2)  // W_16^(4 S) = -S i is a rotation, not a multiplication
+      v[4 * k1 + n2] = n2 * k1 == 4 ? rot<S>(v[4 * k1 + n2]) : cmul(v[4 * k1 + n2], w16<S>(n2 * k1));
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);  // over n2
 }
