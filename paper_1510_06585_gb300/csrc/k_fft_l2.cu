@@ -350,14 +350,16 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
   const uint32_t polls = a.wait_polls ? a.wait_polls - 1 : kPolls;
   const uint32_t total = (uint32_t)fsch_total(a.sc);
   bool failed = false;
-  // Thread 0 claims the next ticket when an item starts, and decodes it and waits for its inputs
-  // when the item ends, so the claim's round trip overlaps the item. The smallest unfinished
-  // ticket is always some CTA's current item (a CTA's next ticket is larger than its current one),
-  // and its inputs are complete, so the grid progresses.
+  // Thread kSched (lane 0 of warp 1) claims the next ticket when an item starts, and decodes it and
+  // waits for its inputs when the item ends; thread 0 releases the finished item at the same time,
+  // so the two round trips overlap. The smallest unfinished ticket is always some CTA's current
+  // item (a CTA's claimed ticket is larger than its current one), and its inputs are complete, so
+  // the grid progresses.
+  constexpr int kSched = 32;
   uint32_t next = 0;
-  if (tid == 0) next = atomicAdd(a.ticket, 1u);
+  if (tid == kSched) next = atomicAdd(a.ticket, 1u);
   for (int it = 0;; ++it) {
-    if (tid == 0) {
+    if (tid == kSched) {
       const Work wk = take(a, next, total);
       const unsigned int *dep = wk.p >= 0 ? dep_of(a, wk) : nullptr;
       if (dep && !wait_count(dep, kJ, polls)) failed = true;
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
     __syncthreads();
     const Work wk = work[it & 1];
     if (wk.p < 0) break;
-    if (tid == 0) next = atomicAdd(a.ticket, 1u);
+    if (tid == kSched) next = atomicAdd(a.ticket, 1u);
     if (wk.p & 1) row_item(a, sm, wk, sm.d, [] {});
     else col_item(a, sm, wk, sm.d, [] {});
     __syncthreads();  // every thread's stores of the item precede the release below
