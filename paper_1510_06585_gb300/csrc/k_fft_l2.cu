@@ -276,7 +276,7 @@ __device__ __forceinline__ void row_last_store(const FftL2Args &a, const Work &w
 // (decimation in time, sign index p - 1) and the line half of transform p + 1 (decimation in
 // frequency, sign index p) with its twiddle W_N^(S n2 k1). A last phase writes X[l + 256 k2] in
 // natural order through shared memory. `hook` runs once, after the loads are issued.
-template <class Hook>
+template <bool Odd, class Hook>
 __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Work &wk, float2 *d, Hook hook) {
   const int tid = threadIdx.x, h = tid >> 4, t = tid & 15;
   const int p = wk.p, j = wk.j;
@@ -309,7 +309,7 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
     for (int k = 0; k < 16; ++k) __stcg(dst + 16 * k, v[k]);
     return;
   }
-  row_last_store(a, wk, d, v);
+  if constexpr (Odd) row_last_store(a, wk, d, v);  // only an odd chain ends on lines
 }
 
 // Thread 0: the work item of ticket `t`, claiming further tickets past those that name no row
@@ -331,6 +331,9 @@ __device__ __forceinline__ const unsigned int *dep_of(const FftL2Args &a, const 
   if (wk.f >= a.ring_rows) return a.done + (wk.f - a.ring_rows) * P + (P - 1);
   return nullptr;
 }
+// Odd: the chain has an odd number of transforms, so its last phase is a line phase (the even
+// chains' kernel leaves that path out, which relieves its registers).
+template <bool Odd>
 __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ FftL2Args a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
     const Work wk = work[it & 1];
     if (wk.p < 0) break;
     if (tid == kSched) next = atomicAdd(a.ticket, 1u);
-    if (wk.p & 1) row_item(a, sm, wk, sm.d, [] {});
+    if (wk.p & 1) row_item<Odd>(a, sm, wk, sm.d, [] {});
     else col_item(a, sm, wk, sm.d, [] {});
     __syncthreads();  // every thread's stores of the item precede the release below
     if (tid == 0)
@@ -391,11 +394,15 @@ int fft_l2_ctas_per_sm() {
     return 0;
   }
   if (init[dev].load()) return cached[dev].load();
-  int n = 0;
-  if (cudaFuncSetAttribute(fft_l2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) !=
+  int n = 0, n1 = 0;
+  if (cudaFuncSetAttribute(fft_l2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft_l2_kernel, kT, sizeof(Smem)) != cudaSuccess)
-    n = 0;
+      cudaFuncSetAttribute(fft_l2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft_l2_kernel<false>, kT, sizeof(Smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, fft_l2_kernel<true>, kT, sizeof(Smem)) != cudaSuccess)
+    n = n1 = 0;
+  n = std::min(n, n1);  // both instantiations are sized by the same grid
   cudaGetLastError();
   cached[dev].store(n);
   init[dev].store(true);
@@ -463,11 +470,14 @@ cudaError_t launch_fft_l2(const FftL2Args &a, int ctas, cudaStream_t s) {
   if (a.nsteps < 1 || a.nsteps > kFftMaxSteps || a.sc.P != a.nsteps + 1 || a.sc.nfft < 1 || ctas < 1 ||
       a.ring_rows < 1 || !a.ring || !a.done || a.ticket != a.done + a.sc.nfft * a.sc.P)
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fft_l2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  const bool odd = a.nsteps & 1;
+  cudaError_t e = cudaFuncSetAttribute(odd ? (const void *)fft_l2_kernel<true> : (const void *)fft_l2_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e == cudaSuccess)
     e = cudaMemsetAsync(a.done, 0, ((size_t)a.sc.nfft * a.sc.P + 1) * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fft_l2_kernel<<<dim3(ctas), dim3(kT), sizeof(Smem), s>>>(a);
+  if (odd) fft_l2_kernel<true><<<dim3(ctas), dim3(kT), sizeof(Smem), s>>>(a);
+  else fft_l2_kernel<false><<<dim3(ctas), dim3(kT), sizeof(Smem), s>>>(a);
   return cudaGetLastError();
 }
 
