@@ -115,8 +115,10 @@ constexpr int kT = 16 * kB;       // threads per CTA: 16 per column or line
 constexpr int kJ = kFftL2Items;   // items per row and phase
 constexpr uint32_t kPolls = 1u << 21;
 
+constexpr int kLine = 16 * 17;  // a line's 256 values between its two 16-point DFTs, rows padded to 17
+
 struct Smem {
-  float2 d[kB * 256];  // the item's values between the two 16-point DFTs (32 KB)
+  float2 d[kB * kLine];  // the item's values between the two 16-point DFTs (34 KB)
   float2 tw[16][16];   // W_256^(t k) at [k][t], forward sign
   float2 w256[256];    // W_256^e, forward sign
   float2 wlo[2][256];  // W_N^e for e < 256: [0] forward, [1] inverse and divided by N
@@ -159,7 +161,9 @@ __device__ __forceinline__ void col_dft(float2 (&v)[16], const Smem &sm, float2 
 }
 
 // 256-point DFT (sign S) along one line per half warp. Thread t holds in v[m] position t + 16 m; on
-// return v[k] holds output position t + 16 k. The line's 256 values in dl: [o_lo][i ^ o_lo].
+// return v[k] holds output position t + 16 k. The line's 256 values in dl: [o_lo][i], rows of 17
+// (the padding keeps both the row writes and the column reads free of bank conflicts, with the
+// offsets immediate).
 template <int S>
 __device__ __forceinline__ void row_dft(float2 (&v)[16], const Smem &sm, float2 *dl, int t) {
   dft16<S>(v);
@@ -168,11 +172,11 @@ __device__ __forceinline__ void row_dft(float2 (&v)[16], const Smem &sm, float2 
   for (int k = 0; k < 16; ++k) {
     float2 z = v[dft16_slot(k)];
     if (k) z = cmul(z, conj_if(sm.tw[k][t], S < 0));
-    dl[k * 16 + (t ^ k)] = z;
+    dl[k * 17 + t] = z;
   }
   __syncwarp();
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = dl[t * 16 + (i ^ t)];
+  for (int i = 0; i < 16; ++i) v[i] = dl[t * 17 + i];
   dft16<S>(v);
   reorder(v);
 }
@@ -283,7 +287,7 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
   const int l = kB * j + h;
   const bool last = p == a.nsteps, has1 = p < a.nsteps;
   const int s2 = a.sign[p - 1], s1 = has1 ? a.sign[p] : 1;
-  float2 *dl = d + h * 256;
+  float2 *dl = d + h * kLine;
   if (has1) {  // q[k][h] = W_4096^(S k l), written and read by the same half warp
     const uint32_t e = (16u * (uint32_t)t * (uint32_t)l) & (kN - 1);
     sm.q[t][h] = s1 > 0 ? wn<1>(sm, e, false) : wn<-1>(sm, e, false);
