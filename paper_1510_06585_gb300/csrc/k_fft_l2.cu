@@ -32,6 +32,7 @@
 // memory: in column items across the CTA's 8 warps, in line items inside a half warp's line.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "fft_ops.cuh"
@@ -119,18 +120,8 @@ constexpr int kLine = 16 * 17;  // a line's 256 values between its two 16-point 
 
 struct Smem {
   float2 d[kB * kLine];  // the item's values between the two 16-point DFTs (34 KB)
-  float2 tw[16][16];   // W_256^(t k) at [k][t], forward sign
-  float2 w256[256];    // W_256^e, forward sign
-  float2 wlo[2][256];  // W_N^e for e < 256: [0] forward, [1] inverse and divided by N
-  float2 q[16][kB];    // W_4096^(S k u) for the item's columns or lines u, k < 16
+  float2 tw[16][16];     // W_256^(t k) at [k][t], forward sign
 };
-
-// W_N^(S e) for 0 <= e < N, divided by N when S < 0 and `scaled`: W_N^e = W_N^(e mod 256) W_256^(e / 256).
-template <int S>
-__device__ __forceinline__ float2 wn(const Smem &sm, uint32_t e, bool scaled) {
-  const float2 lo = S > 0 ? sm.wlo[0][e & 255] : (scaled ? sm.wlo[1][e & 255] : conj_if(sm.wlo[0][e & 255], true));
-  return cmul(lo, conj_if(sm.w256[e >> 8], S < 0));
-}
 
 __device__ __forceinline__ void reorder(float2 (&v)[16]) {
   float2 t[16];
@@ -214,10 +205,6 @@ __device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Wor
   const int b = kB * j + lane;
   const bool last = p == a.nsteps, has2 = p >= 1, has1 = p < a.nsteps;
   const int s2 = has2 ? a.sign[p - 1] : 1, s1 = has1 ? a.sign[p] : 1;
-  if (has1) {  // q[k][lane] = W_4096^(S b k)
-    const uint32_t e = (16u * (uint32_t)b * (uint32_t)w) & (kN - 1);
-    sm.q[w][lane] = s1 > 0 ? wn<1>(sm, e, false) : wn<-1>(sm, e, false);
-  }
   const float2 *src = item_src(a, wk) + b;
   float2 v[16];
   if (p == 0) {
@@ -237,10 +224,9 @@ __device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Wor
   if (has1) {
     if (s1 > 0) col_dft<1>(v, sm, d, w, lane);
     else col_dft<-1>(v, sm, d, w, lane);
-    const uint32_t e = (uint32_t)b * (uint32_t)w;  // W_N^(S b (w + 16 k)) = W_N^(S b w) W_4096^(S b k)
-    const float2 base = s1 > 0 ? wn<1>(sm, e, true) : wn<-1>(sm, e, true);
+    const float2 *tw = (s1 > 0 ? a.twiddle : a.twiddle + kN) + b;  // W_N^(S k1 b) at [k1][b]
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = cmul(cmul(v[k], base), sm.q[k][lane]);
+    for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(tw + (w + 16 * k) * 256));
   }
   if (last) {
     float2 *dst = a.out + wk.f * kN + b;
@@ -288,10 +274,6 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
   const bool last = p == a.nsteps, has1 = p < a.nsteps;
   const int s2 = a.sign[p - 1], s1 = has1 ? a.sign[p] : 1;
   float2 *dl = d + h * kLine;
-  if (has1) {  // q[k][h] = W_4096^(S k l), written and read by the same half warp
-    const uint32_t e = (16u * (uint32_t)t * (uint32_t)l) & (kN - 1);
-    sm.q[t][h] = s1 > 0 ? wn<1>(sm, e, false) : wn<-1>(sm, e, false);
-  }
   const float2 *src = item_src(a, wk) + (int64_t)l * 256 + t;
   float2 v[16];
 #pragma unroll
@@ -302,10 +284,9 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
   if (has1) {
     if (s1 > 0) row_dft<1>(v, sm, dl, t);
     else row_dft<-1>(v, sm, dl, t);
-    const uint32_t e = (uint32_t)t * (uint32_t)l;  // W_N^(S (t + 16 k) l) = W_N^(S t l) W_4096^(S k l)
-    const float2 base = s1 > 0 ? wn<1>(sm, e, true) : wn<-1>(sm, e, true);
+    const float2 *tw = (s1 > 0 ? a.twiddle : a.twiddle + kN) + (int64_t)l * 256 + t;  // W_N^(S l n2)
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = cmul(cmul(v[k], base), sm.q[k][h]);
+    for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(tw + 16 * k));
   }
   if (!last) {
     float2 *dst = a.ring + (wk.f % a.ring_rows) * kN + (int64_t)l * 256 + t;
@@ -343,16 +324,11 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   __shared__ Work work[2];
   const int tid = threadIdx.x;
-  // twiddle tables: W_M^e = (cos(2 pi e / M), -sin(2 pi e / M)), exact integer exponents
+  // W_256^(t k) = (cos(2 pi t k / 256), -sin(2 pi t k / 256)), exact integer exponents
   for (int e = tid; e < 256; e += kT) {
     float sn, cs;
-    sincospif((float)e / 128.f, &sn, &cs);
-    sm.w256[e] = make_float2(cs, -sn);
     sincospif((float)((e >> 4) * (e & 15)) / 128.f, &sn, &cs);
     sm.tw[e >> 4][e & 15] = make_float2(cs, -sn);
-    sincospif((float)e / 32768.f, &sn, &cs);
-    sm.wlo[0][e] = make_float2(cs, -sn);
-    sm.wlo[1][e] = make_float2(cs * (1.f / kN), sn * (1.f / kN));
   }
   const uint32_t polls = a.wait_polls ? a.wait_polls - 1 : kPolls;
   const uint32_t total = (uint32_t)fsch_total(a.sc);
@@ -385,9 +361,53 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
   if (failed && a.status) *(volatile unsigned int *)a.status = 1u;
 }
 
+// The four-step twiddles of every launch: [0, N) holds W_N^(k1 b) at [k1][b] (k1, b < 256), and
+// [N, 2N) the inverse, conj(W_N^(k1 b)) / N, so a half warp reads 16 consecutive values of one k1.
+__global__ void fft_l2_twiddle_kernel(float2 *t) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint32_t)kN) return;
+  const uint32_t e = ((i >> 8) * (i & 255)) & (kN - 1);
+  float sn, cs;
+  sincospif((float)e / (float)(kN / 2), &sn, &cs);
+  t[i] = make_float2(cs, -sn);
+  t[kN + i] = make_float2(cs * (1.f / kN), sn * (1.f / kN));
+}
+
 }  // namespace
 
 size_t fft_l2_smem_bytes() { return sizeof(Smem); }
+
+// Built once per device, on a private stream, and kept until the process exits (1 MB); the first
+// call on a device allocates, so it cannot be part of a stream capture.
+cudaError_t fft_l2_twiddles(const float2 **out) {
+  static std::mutex mu;
+  static float2 *tables[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tables[dev]) {
+    float2 *t = nullptr;
+    e = cudaMalloc(&t, 2 * (size_t)kN * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    cudaStream_t st = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      fft_l2_twiddle_kernel<<<kN / 256, 256, 0, st>>>(t);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    if (e != cudaSuccess) {
+      cudaFree(t);
+      return e;
+    }
+    tables[dev] = t;
+  }
+  *out = tables[dev];
+  return cudaSuccess;
+}
 
 int fft_l2_ctas_per_sm() {
   static std::atomic<int> cached[64];

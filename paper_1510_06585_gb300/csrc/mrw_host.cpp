@@ -2157,6 +2157,7 @@ mrw_status enqueue_fft_l2(Launch &L, const Program &p, const float2 *dx, float2 
   a.done = (unsigned int *)((char *)ws + ring_padded);
   a.status = status;
   a.wait_polls = test_wait_polls();
+  CU(fft_l2_twiddles(&a.twiddle));
   if (status) *used_status = true;
   for (size_t i = 0, c = 0; i < p.fft.size(); i += per, ++c) {
     const FftL2Plan &pl = plans[c];

@@ -278,6 +278,7 @@ struct FftL2Args {
   unsigned int *done;      // nfft * P completion counters, zeroed by launch_fft_l2
   unsigned int *ticket;    // == done + nfft * P, zeroed with them
   unsigned int *status;    // set to 1 if a bounded wait gave up (may be null)
+  const float2 *twiddle;   // fft_l2_twiddles: W_N^(k1 b) at [k1][b], then its inverse / N
   FftSched sc;
   int64_t ring_rows;
   int32_t nsteps;
@@ -292,6 +293,8 @@ struct FftL2Plan {
   size_t counter_bytes;    // nfft * P + 1 counters
 };
 size_t fft_l2_smem_bytes();
+// The per-device four-step twiddle table of the L2-ring kernel (built on first use, 1 MB, kept).
+cudaError_t fft_l2_twiddles(const float2 **out);
 int fft_l2_ctas_per_sm();  // resident CTAs per SM on the current device (0: cannot launch)
 bool fft_l2_plan(int64_t nfft, int nsteps, int ctas, FftL2Plan *out);
 bool fft_l2_schedule_ok(const FftSched &c, int64_t ring_rows);
