@@ -131,11 +131,33 @@ __device__ __forceinline__ void reorder(float2 (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = t[k];
 }
 
+// The output of a 256-point DFT times the four-step twiddles post[k * stride] (TW), whose loads are
+// issued once the first 16-point DFT's values have gone to shared memory, so that they travel
+// while the second one runs.
+template <bool TW>
+struct Post {
+  const float2 *p;
+  int stride;
+  float2 v[TW ? 16 : 1];
+  __device__ __forceinline__ void load() {
+    if constexpr (TW) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = __ldg(p + k * stride);
+    }
+  }
+  __device__ __forceinline__ void apply(float2 (&x)[16]) const {
+    if constexpr (TW) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) x[k] = cmul(x[k], v[k]);
+    }
+  }
+};
+
 // 256-point DFT (sign S) down the item's kB columns. Thread (w, lane) holds in v[m] row w + 16 m of
 // column lane; on return v[k] holds output row w + 16 k. Layout of d between the two 16-point
 // DFTs: [o_lo][w][lane], a half warp's 16 values contiguous in every access.
-template <int S>
-__device__ __forceinline__ void col_dft(float2 (&v)[16], const Smem &sm, float2 *d, int w, int lane) {
+template <int S, bool TW>
+__device__ __forceinline__ void col_dft(float2 (&v)[16], const Smem &sm, float2 *d, int w, int lane, Post<TW> post) {
   dft16<S>(v);      // over m: output o_lo in v[dft16_slot(o_lo)]
   __syncthreads();  // the buffer's previous contents have been read
 #pragma unroll
@@ -144,19 +166,21 @@ __device__ __forceinline__ void col_dft(float2 (&v)[16], const Smem &sm, float2 
     if (k) z = cmul(z, conj_if(sm.tw[k][w], S < 0));
     d[(k * 16 + w) * kB + lane] = z;
   }
+  post.load();
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = d[(w * 16 + i) * kB + lane];
   dft16<S>(v);  // over the first index: output o_hi
   reorder(v);
+  post.apply(v);
 }
 
 // 256-point DFT (sign S) along one line per half warp. Thread t holds in v[m] position t + 16 m; on
 // return v[k] holds output position t + 16 k. The line's 256 values in dl: [o_lo][i], rows of 17
 // (the padding keeps both the row writes and the column reads free of bank conflicts, with the
 // offsets immediate).
-template <int S>
-__device__ __forceinline__ void row_dft(float2 (&v)[16], const Smem &sm, float2 *dl, int t) {
+template <int S, bool TW>
+__device__ __forceinline__ void row_dft(float2 (&v)[16], const Smem &sm, float2 *dl, int t, Post<TW> post) {
   dft16<S>(v);
   __syncwarp();  // the line's previous contents have been read
 #pragma unroll
@@ -165,11 +189,13 @@ __device__ __forceinline__ void row_dft(float2 (&v)[16], const Smem &sm, float2 
     if (k) z = cmul(z, conj_if(sm.tw[k][t], S < 0));
     dl[k * 17 + t] = z;
   }
+  post.load();
   __syncwarp();
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = dl[t * 17 + i];
   dft16<S>(v);
   reorder(v);
+  post.apply(v);
 }
 
 __device__ __forceinline__ bool wait_count(const unsigned int *c, unsigned int want, uint32_t polls) {
@@ -216,17 +242,16 @@ __device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Wor
   }
   hook();  // runs while the loads are in flight
   if (has2) {
-    if (s2 > 0) col_dft<1>(v, sm, d, w, lane);
-    else col_dft<-1>(v, sm, d, w, lane);
+    if (s2 > 0) col_dft<1>(v, sm, d, w, lane, Post<false>{});
+    else col_dft<-1>(v, sm, d, w, lane, Post<false>{});
   }
   if (last)  // every thread's loads were consumed before the barriers above: drop the ring lines
     for (int r = tid; r < 256; r += kT) discard_l2(item_src(a, wk) + r * 256 + kB * j);  // from L2 unwritten
   if (has1) {
-    if (s1 > 0) col_dft<1>(v, sm, d, w, lane);
-    else col_dft<-1>(v, sm, d, w, lane);
-    const float2 *tw = (s1 > 0 ? a.twiddle : a.twiddle + kN) + b;  // W_N^(S k1 b) at [k1][b]
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(tw + (w + 16 * k) * 256));
+    // W_N^(S k1 b) at [k1][b], k1 = w + 16 k
+    const Post<true> tw{(s1 > 0 ? a.twiddle : a.twiddle + kN) + w * 256 + b, 16 * 256, {}};
+    if (s1 > 0) col_dft<1>(v, sm, d, w, lane, tw);
+    else col_dft<-1>(v, sm, d, w, lane, tw);
   }
   if (last) {
     float2 *dst = a.out + wk.f * kN + b;
@@ -279,14 +304,13 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = __ldcg(src + 16 * m);
   hook();  // runs while the loads are in flight
-  if (s2 > 0) row_dft<1>(v, sm, dl, t);
-  else row_dft<-1>(v, sm, dl, t);
+  if (s2 > 0) row_dft<1>(v, sm, dl, t, Post<false>{});
+  else row_dft<-1>(v, sm, dl, t, Post<false>{});
   if (has1) {
-    if (s1 > 0) row_dft<1>(v, sm, dl, t);
-    else row_dft<-1>(v, sm, dl, t);
-    const float2 *tw = (s1 > 0 ? a.twiddle : a.twiddle + kN) + (int64_t)l * 256 + t;  // W_N^(S l n2)
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(tw + 16 * k));
+    // W_N^(S l n2) at [l][n2], n2 = t + 16 k
+    const Post<true> tw{(s1 > 0 ? a.twiddle : a.twiddle + kN) + (int64_t)l * 256 + t, 16, {}};
+    if (s1 > 0) row_dft<1>(v, sm, dl, t, tw);
+    else row_dft<-1>(v, sm, dl, t, tw);
   }
   if (!last) {
     float2 *dst = a.ring + (wk.f % a.ring_rows) * kN + (int64_t)l * 256 + t;
