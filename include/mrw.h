@@ -247,7 +247,8 @@ void mrw_node_release(mrw_node_t n);
  *     on such a cluster, two CTAs per SM; with more rows, a persistent grid splits every row into
  *     work items (16 columns or 16 lines of its 256 x 256 four-step matrix) whose values wait
  *     between phases in an L2-resident ring (a few tens of MB of device scratch per call; see
- *     mrw_fft_schedule_check). cfg->ctas_per_sm 1 asks for that form, 2 for the cluster form, 4
+ *     mrw_fft_schedule_check; the first such call on a device also builds a 1 MB twiddle table
+ *     that is kept until exit, so that call cannot be part of a stream capture). cfg->ctas_per_sm 1 asks for that form, 2 for the cluster form, 4
  *     for clusters of 8 with the exchange's values in tensor memory (three CTAs per SM), 3 for
  *     clusters of 16 CTAs (where the device allows that cluster size).
  * Every args[i] may be device or host memory (mrw_buffer.memory). The call is asynchronous:
