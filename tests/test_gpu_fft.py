@@ -43,16 +43,20 @@ def test_pipelines_match_the_oracle_fused_and_per_stage(names):
         assert F.rel_error(got, want) <= TOL, (names, cfg.fusion, F.rel_error(got, want))
 
 
-def test_closed_forms():
+@pytest.mark.parametrize("cps", [0, 1])  # the default (a cluster per row at 3 rows) and the L2-ring form
+def test_closed_forms(cps):
     x = np.zeros((3, N), np.complex64)
     x[0, 0] = 1.0                                              # impulse -> all ones
     k0 = 4321
     x[1] = np.exp(2j * np.pi * k0 * np.arange(N) / N)          # exponential -> N at k0
     x[2] = 0.75 - 0.25j                                        # constant -> N (0.75 - 0.25i) at 0
-    X = run(tree_of(["fft"]), x).astype(np.complex128)
+    X = run(tree_of(["fft"]), x, M.config(ctas_per_sm=cps)).astype(np.complex128)
     assert np.abs(X[0] - 1.0).max() <= 1e-6
     assert abs(X[1, k0] - N) <= 1e-3 * N ** 0.5 and np.abs(np.delete(X[1], k0)).max() <= 1e-3 * N ** 0.5
     assert abs(X[2, 0] - N * (0.75 - 0.25j)) <= 1e-3 and np.abs(X[2, 1:]).max() <= 1e-3
+    # the inverse of the impulse's transform is the impulse: N^-1 sum_k e^(+2 pi i k n / N) = [n = 0]
+    y = run(tree_of(["ifft"]), X[:1].astype(np.complex64), M.config(ctas_per_sm=cps)).astype(np.complex128)
+    assert abs(y[0, 0] - 1.0) <= 1e-6 and np.abs(y[0, 1:]).max() <= 1e-6
 
 
 def test_forward_then_inverse_returns_the_input_and_matches_per_stage():
