@@ -222,10 +222,8 @@ __device__ __forceinline__ const float2 *item_src(const FftL2Args &a, const Work
 
 // One column item: columns [kB j, kB j + kB) of row f in phase p (p even). The phase holds the
 // column half of transform p (decimation in frequency, sign index p - 1) and the column half of
-// transform p + 1 (decimation in time, sign index p) with its twiddle W_N^(S b k1). `hook` runs
-// once, after the loads are issued.
-template <class Hook>
-__device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Work &wk, float2 *d, Hook hook) {
+// transform p + 1 (decimation in time, sign index p) with its twiddle W_N^(S b k1).
+__device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Work &wk, float2 *d) {
   const int tid = threadIdx.x, w = tid / kB, lane = tid % kB;
   const int p = wk.p, j = wk.j;
   const int b = kB * j + lane;
@@ -240,7 +238,6 @@ __device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Wor
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = __ldcg(src + (w + 16 * m) * 256);
   }
-  hook();  // runs while the loads are in flight
   if (has2) {
     if (s2 > 0) col_dft<1>(v, sm, d, w, lane, Post<false>{});
     else col_dft<-1>(v, sm, d, w, lane, Post<false>{});
@@ -290,9 +287,9 @@ __device__ __forceinline__ void row_last_store(const FftL2Args &a, const Work &w
 // line, its values in d as [line][position]. The phase holds the line half of transform p
 // (decimation in time, sign index p - 1) and the line half of transform p + 1 (decimation in
 // frequency, sign index p) with its twiddle W_N^(S n2 k1). A last phase writes X[l + 256 k2] in
-// natural order through shared memory. `hook` runs once, after the loads are issued.
-template <bool Odd, class Hook>
-__device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Work &wk, float2 *d, Hook hook) {
+// natural order through shared memory.
+template <bool Odd>
+__device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Work &wk, float2 *d) {
   const int tid = threadIdx.x, h = tid >> 4, t = tid & 15;
   const int p = wk.p, j = wk.j;
   const int l = kB * j + h;
@@ -303,7 +300,6 @@ __device__ __forceinline__ void row_item(const FftL2Args &a, Smem &sm, const Wor
   float2 v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = __ldcg(src + 16 * m);
-  hook();  // runs while the loads are in flight
   if (s2 > 0) row_dft<1>(v, sm, dl, t, Post<false>{});
   else row_dft<-1>(v, sm, dl, t, Post<false>{});
   if (has1) {
@@ -376,8 +372,8 @@ __global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ F
     const Work wk = work[it & 1];
     if (wk.p < 0) break;
     if (tid == kSched) next = atomicAdd(a.ticket, 1u);
-    if (wk.p & 1) row_item<Odd>(a, sm, wk, sm.d, [] {});
-    else col_item(a, sm, wk, sm.d, [] {});
+    if (wk.p & 1) row_item<Odd>(a, sm, wk, sm.d);
+    else col_item(a, sm, wk, sm.d);
     __syncthreads();  // every thread's stores of the item precede the release below
     if (tid == 0)
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + wk.f * a.sc.P + wk.p) : "memory");
