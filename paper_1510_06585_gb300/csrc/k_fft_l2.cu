@@ -156,10 +156,12 @@ struct Post {
 // 256-point DFT (sign S) down the item's kB columns. Thread (w, lane) holds in v[m] row w + 16 m of
 // column lane; on return v[k] holds output row w + 16 k. Layout of d between the two 16-point
 // DFTs: [o_lo][w][lane], a half warp's 16 values contiguous in every access.
-template <int S, bool TW>
+// Fresh: the item's first transform (the barriers between items already order the buffer's
+// previous contents before it).
+template <int S, bool TW, bool Fresh>
 __device__ __forceinline__ void col_dft(float2 (&v)[16], const Smem &sm, float2 *d, int w, int lane, Post<TW> post) {
-  dft16<S>(v);      // over m: output o_lo in v[dft16_slot(o_lo)]
-  __syncthreads();  // the buffer's previous contents have been read
+  dft16<S>(v);  // over m: output o_lo in v[dft16_slot(o_lo)]
+  if constexpr (!Fresh) __syncthreads();  // the buffer's previous contents have been read
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     float2 z = v[dft16_slot(k)];
@@ -239,16 +241,21 @@ __device__ __forceinline__ void col_item(const FftL2Args &a, Smem &sm, const Wor
     for (int m = 0; m < 16; ++m) v[m] = __ldcg(src + (w + 16 * m) * 256);
   }
   if (has2) {
-    if (s2 > 0) col_dft<1>(v, sm, d, w, lane, Post<false>{});
-    else col_dft<-1>(v, sm, d, w, lane, Post<false>{});
+    if (s2 > 0) col_dft<1, false, true>(v, sm, d, w, lane, Post<false>{});
+    else col_dft<-1, false, true>(v, sm, d, w, lane, Post<false>{});
   }
   if (last)  // every thread's loads were consumed before the barriers above: drop the ring lines
     for (int r = tid; r < 256; r += kT) discard_l2(item_src(a, wk) + r * 256 + kB * j);  // from L2 unwritten
   if (has1) {
     // W_N^(S k1 b) at [k1][b], k1 = w + 16 k
     const Post<true> tw{(s1 > 0 ? a.twiddle : a.twiddle + kN) + w * 256 + b, 16 * 256, {}};
-    if (s1 > 0) col_dft<1>(v, sm, d, w, lane, tw);
-    else col_dft<-1>(v, sm, d, w, lane, tw);
+    if (has2) {
+      if (s1 > 0) col_dft<1, true, false>(v, sm, d, w, lane, tw);
+      else col_dft<-1, true, false>(v, sm, d, w, lane, tw);
+    } else {
+      if (s1 > 0) col_dft<1, true, true>(v, sm, d, w, lane, tw);
+      else col_dft<-1, true, true>(v, sm, d, w, lane, tw);
+    }
   }
   if (last) {
     float2 *dst = a.out + wk.f * kN + b;
