@@ -346,7 +346,7 @@ __device__ __forceinline__ const unsigned int *dep_of(const FftL2Args &a, const 
 // Odd: the chain has an odd number of transforms, so its last phase is a line phase (the even
 // chains' kernel leaves that path out, which relieves its registers).
 template <bool Odd>
-__global__ void __launch_bounds__(kT, 3) fft_l2_kernel(const __grid_constant__ FftL2Args a) {
+__global__ void __launch_bounds__(kT, 4) fft_l2_kernel(const __grid_constant__ FftL2Args a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   __shared__ Work work[2];
