@@ -19,17 +19,20 @@
 // the transposed result back in natural order through shared memory).
 //
 // Work items: phase p of row f is 16 items of 16 columns (column phases) or 16 lines (line phases),
-// 4096 values each, one CTA of 256 threads per item. Between phases a row's values wait in its
-// slot of the ring; an item's 32 KB is read and written in 128-byte pieces per half warp. Each CTA of a persistent grid claims tickets from a
-// global counter; the ticket order puts phase p of a slice of rows L steps after phase p - 1, so an
-// item's inputs are usually complete when it is claimed, and a per-row, per-phase completion
-// counter (acquire / release, a bounded wait) guards the rest. Every dependency of a ticket lies on
-// a smaller ticket, claimed by a running CTA, so the grid always progresses. The last phase of a
-// row discards its ring lines from L2 after reading them, so dead values are never written back to
-// HBM. HBM traffic is the input read once and the output written once.
+// 4096 values each, one CTA of 256 threads per item (four CTAs per SM). Between phases a row's
+// values wait in its slot of the ring; an item's 32 KB is read and written in 128-byte pieces per
+// half warp. Each CTA of a persistent grid claims tickets from a global counter; the ticket order
+// puts phase p of a slice of rows L steps after phase p - 1, so an item's inputs are usually
+// complete when it is claimed, and a per-row, per-phase completion counter (acquire / release, a
+// bounded wait) guards the rest. Every dependency of a ticket lies on a smaller ticket, claimed by
+// a running CTA, so the grid always progresses. The last phase of a row discards its ring lines
+// from L2 after reading them, so dead values are never written back to HBM. HBM traffic is the
+// input read once and the output written once; the four-step twiddles come from a per-device
+// 256 x 256 table that stays in L2.
 //
-// A 256-point DFT is two 16-point DFTs in registers (radix 4 x 4) with one transpose through shared
-// memory: in column items across the CTA's 8 warps, in line items inside a half warp's line.
+// A 256-point DFT is two 16-point DFTs in registers (radix 4 x 4, the 4-point butterflies in paired
+// f32x2 instructions) with one transpose through shared memory: in column items across the CTA's
+// 8 warps, in line items inside a half warp's line.
 #include <algorithm>
 #include <atomic>
 #include <mutex>

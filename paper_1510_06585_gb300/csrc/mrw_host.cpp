@@ -2115,9 +2115,10 @@ mrw_status validate_fft_args(const mrw_buffer *args, int nargs, View *vx, View *
 // registers (two CTAs per SM; 36 clusters at once on GB300) or in TMEM (three per SM; 51
 // clusters); the L2-ring form splits each row's phases into work items of a persistent grid and
 // exchanges the values through an L2-resident ring. Every row of a cluster form runs at once up to
-// the clusters' residency, and there the register form's row is the shortest (26 against 31 us for
-// a forward and inverse pair of 16 rows); beyond it the L2-ring form is the fastest measured (48 us
-// at 64 rows, 159 at 256, 307 at 512, against 50, 182 and 360 for the TMEM form). The default takes
+// the clusters' residency, and there the forms are within a few microseconds of each other (the
+// register form ahead at 4-12 rows and for single transforms, the ring form for pairs of 16-36
+// rows); beyond it the L2-ring form is the fastest measured (41 us for a forward and inverse pair
+// of 64 rows, 125 at 256, 236 at 512, against 48, 174 and 340 for the TMEM form). The default takes
 // the L2-ring form exactly when nfft exceeds the register form's residency. cfg.ctas_per_sm 1 asks
 // for the L2-ring form, 2 for the register form, 4 for the TMEM form and 3 for clusters of 16 CTAs
 // (three per SM, where the device allows that cluster size).
