@@ -180,3 +180,21 @@ print("after", F.rel_error(yd.cpu().numpy(), x) <= 1e-5)
     assert r.returncode == 0, r.stderr
     assert "status %d" % M.MRW_ERR_DEVICE in r.stdout, r.stdout
     assert "after True" in r.stdout, r.stdout
+
+
+def test_ring_form_reuses_its_slots_many_times():
+    # 700 rows: about six times the ring's rows, so most rows wait for the row that last held their
+    # slot; every row of the pair comes back to its input, and sampled rows of a single transform
+    # match the oracle
+    x = inputs.fft_signals(700, N, seed=17)
+    ring = M.config(ctas_per_sm=1)
+    d = M.plan_describe(tree_of(["fft", "ifft"]), [torch.zeros(700, N, dtype=torch.complex64, device="cuda")] * 2, ring)
+    assert d["form"] == "l2" and d["schedule_ok"] and 700 >= 5 * d["ring_rows"], d
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    M.execute(tree_of(["fft", "ifft"]), [xd, yd], ring).wait(120000)
+    y = yd.cpu().numpy()
+    assert max(F.rel_error(y[i:i + 100], x[i:i + 100]) for i in range(0, 700, 100)) <= TOL
+    M.execute(tree_of(["fft"]), [xd, yd], ring).wait(120000)
+    rows = [0, 111, 112, 350, 699]
+    assert F.rel_error(yd.cpu().numpy()[rows], F.fft_rows(x[rows])) <= TOL
